@@ -1,0 +1,51 @@
+"""FP64 listmode OSEM and log-likelihood gradient on top of the oracle
+projector.  TEST INFRASTRUCTURE ONLY (see package docstring).
+
+Listmode OSEM (paper Sec. 2.6 and 3, Fig. 6 caption): with sensitivity image
+s = A^T 1 over all possible LORs, subset S of n_sub event subsets, additive
+background b and unit event values,
+    x <- x / (s / n_sub) * A_S^T ( 1 / (A_S x + b) ),   x = 0 where s = 0.
+Subset m holds the events e with e mod n_sub == m.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import joseph
+
+
+def _subset(arrs, m, n_sub):
+    return [None if a is None else np.asarray(a)[m::n_sub] for a in arrs]
+
+
+def lm_osem_subset_update(x, xs, xe, tof_bin, geom, tof, sens, b, m, n_sub, threads=1):
+    """One subset update of TOF listmode OSEM (double precision)."""
+    sxs, sxe, stb = _subset([xs, xe, tof_bin], m, n_sub)
+    p = joseph.fwd(sxs, sxe, x, geom, mode="tof_lm", tof=tof, tof_bin=stb, threads=threads)
+    q = 1.0 / (p + b)
+    bp = joseph.back(sxs, sxe, q, geom, mode="tof_lm", tof=tof, tof_bin=stb, threads=threads)
+    s = np.asarray(sens, dtype=np.float64) / n_sub
+    out = np.zeros_like(np.asarray(x, dtype=np.float64))
+    pos = s > 0
+    out[pos] = np.asarray(x, dtype=np.float64)[pos] * bp[pos] / s[pos]
+    return out
+
+
+def lm_osem(xs, xe, tof_bin, geom, tof, sens, b, n_iter, n_sub, threads=1, x0=None):
+    """Full TOF listmode OSEM: x0 = 1 on voxels with s > 0 (else 0)."""
+    sens = np.asarray(sens, dtype=np.float64)
+    x = (sens > 0).astype(np.float64) if x0 is None else np.asarray(x0, dtype=np.float64).copy()
+    for _ in range(n_iter):
+        for m in range(n_sub):
+            x = lm_osem_subset_update(x, xs, xe, tof_bin, geom, tof, sens, b, m, n_sub, threads)
+    return x
+
+
+def poisson_loglik_grad(x, xs, xe, tof_bin, geom, tof, w, b, threads=1):
+    """f(x) = sum_e w_e log((A x)_e + b) and its gradient A^T (w / (A x + b))."""
+    p = joseph.fwd(xs, xe, x, geom, mode="tof_lm", tof=tof, tof_bin=tof_bin, threads=threads)
+    w = np.asarray(w, dtype=np.float64)
+    val = float(np.sum(w * np.log(p + b)))
+    g = joseph.back(xs, xe, w / (p + b), geom, mode="tof_lm", tof=tof, tof_bin=tof_bin,
+                    threads=threads)
+    return val, g

@@ -1,0 +1,533 @@
+"""Pins for the FP64 oracle (CPU only).
+
+Each test checks the oracle against something other than itself: hand-derived
+values, closed forms, brute force through an independent formulation,
+invariants (adjoint, symmetry, translation, partition of unity) and numerical
+quadrature.  ``test_planted_mistakes_are_caught`` rebuilds the oracle with
+plausible errors planted in it and shows that the pins catch every one.
+"""
+import json
+import math
+import os
+from fractions import Fraction
+from types import SimpleNamespace
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2212_12519_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def G(shape, origin, vox):
+    return SimpleNamespace(shape=tuple(shape), origin=tuple(origin), voxsize=tuple(vox))
+
+
+def T(bin_width, sigma, n_sigmas, n_bins):
+    return SimpleNamespace(bin_width=bin_width, sigma=sigma, n_sigmas=n_sigmas, n_bins=n_bins)
+
+
+# ---------------------------------------------------------------------------
+# independent formulation (pure Python): tent-function matrix entries
+# ---------------------------------------------------------------------------
+def _principal_axis_exact(xs, xe):
+    d = [abs(Fraction(float(xe[i])) - Fraction(float(xs[i]))) for i in range(3)]
+    m = max(d)
+    return min(i for i in range(3) if d[i] == m)
+
+
+def _tent(t):
+    return max(0.0, 1.0 - abs(t))
+
+
+def _gauss_bin(dist, D, s, ns):
+    if abs(dist) > ns * s + 0.5 * D:
+        return 0.0
+    k = 1.0 / (math.sqrt(2.0) * s)
+    return 0.5 * (math.erf((dist + 0.5 * D) * k) - math.erf((dist - 0.5 * D) * k))
+
+
+def dense_tent(xs, xe, geom, mode="nontof", tof=None, tof_bin=None):
+    """A[row, voxel] = w0 * sum_k [k == voxel_a] tent(u_k - i_b) tent(w_k - i_c) (* TOF)."""
+    n = geom.shape
+    o = geom.origin
+    v = geom.voxsize
+    nrow_per = tof.n_bins if mode == "tof_sino" else 1
+    A = np.zeros((len(xs) * nrow_per, int(np.prod(n))))
+    for r, (p, q) in enumerate(zip(np.asarray(xs, np.float64), np.asarray(xe, np.float64))):
+        d = q - p
+        L = math.sqrt(float(np.dot(d, d)))
+        if L == 0:
+            continue
+        a = _principal_axis_exact(p, q)
+        b, c = [i for i in range(3) if i != a]
+        w0 = v[a] * L / abs(d[a])
+        for k in range(n[a]):
+            X = o[a] + k * v[a]
+            if not (min(p[a], q[a]) <= X <= max(p[a], q[a])):
+                continue
+            t = (X - p[a]) / d[a]
+            Pb = p[b] + t * d[b]
+            Pc = p[c] + t * d[c]
+            u = (Pb - o[b]) / v[b]
+            w = (Pc - o[c]) / v[c]
+            tau = (t - 0.5) * L
+            for ib in range(n[b]):
+                tb = _tent(u - ib)
+                if tb == 0.0:
+                    continue
+                for ic in range(n[c]):
+                    tc = _tent(w - ic)
+                    if tc == 0.0:
+                        continue
+                    ijk = [0, 0, 0]
+                    ijk[a], ijk[b], ijk[c] = k, ib, ic
+                    col = (ijk[0] * n[1] + ijk[1]) * n[2] + ijk[2]
+                    base = w0 * tb * tc
+                    if mode == "nontof":
+                        A[r, col] += base
+                    elif mode == "tof_sino":
+                        for t_ in range(tof.n_bins):
+                            cen = (t_ - (tof.n_bins - 1) / 2.0) * tof.bin_width
+                            A[r * nrow_per + t_, col] += base * _gauss_bin(
+                                tau - cen, tof.bin_width, tof.sigma, tof.n_sigmas)
+                    else:
+                        cen = tof_bin[r] * tof.bin_width
+                        A[r, col] += base * _gauss_bin(tau - cen, tof.bin_width, tof.sigma,
+                                                       tof.n_sigmas)
+    return A
+
+
+def dense_by_fwd(xs, xe, geom, mode="nontof", tof=None, tof_bin=None, mutant=0):
+    nvox = int(np.prod(geom.shape))
+    cols = []
+    for j in range(nvox):
+        e = np.zeros(nvox)
+        e[j] = 1.0
+        cols.append(oracle.fwd(xs, xe, e.reshape(geom.shape), geom, mode=mode, tof=tof,
+                               tof_bin=tof_bin, mutant=mutant).reshape(-1))
+    return np.stack(cols, 1)
+
+
+def dense_by_back(xs, xe, geom, mode="nontof", tof=None, tof_bin=None, mutant=0):
+    nrow_per = tof.n_bins if mode == "tof_sino" else 1
+    nrow = len(xs) * nrow_per
+    rows = []
+    for i in range(nrow):
+        e = np.zeros(nrow)
+        e[i] = 1.0
+        rows.append(oracle.back(xs, xe, e, geom, mode=mode, tof=tof, tof_bin=tof_bin,
+                                mutant=mutant).reshape(-1))
+    return np.stack(rows, 0)
+
+
+# small brute-force geometry: non-isotropic voxels, off-centre origin
+BF_GEOM = G((4, 4, 4), (-1.7, -2.2, -1.1), (1.0, 1.5, 0.75))
+BF_TOF = T(bin_width=1.3, sigma=1.1, n_sigmas=3.0, n_bins=7)
+
+
+def bf_rays():
+    xs, xe = synth.random_lors(24, synth.ImageGeom(BF_GEOM.shape, BF_GEOM.origin, BF_GEOM.voxsize),
+                               seed=11, radius_factor=1.6)
+    extra_s, extra_e = [], []
+    # axis-aligned through voxel centres and between them, each direction
+    extra_s += [(-9.0, -0.7, -0.35), (-0.7, -9.0, 0.4), (0.3, 0.8, -9.0)]
+    extra_e += [(9.0, -0.7, -0.35), (-0.7, 9.0, 0.4), (0.3, 0.8, 9.0)]
+    # exact principal-axis ties with an out-of-plane slope
+    extra_s += [(-6.0, -6.3, -0.9), (-0.2, -5.0, -5.4), (-4.0, 1.0, -4.1)]
+    extra_e += [(6.0, 5.7, 0.8), (0.9, 5.0, 4.6), (4.0, -0.3, 3.9)]
+    # ray ending exactly on a plane centre, inside the image
+    extra_s += [(-9.0, 0.1, 0.2)]
+    extra_e += [(-1.7 + 2.0, 0.9, -0.4)]
+    # degenerate ray
+    extra_s += [(0.1, 0.2, 0.3)]
+    extra_e += [(0.1, 0.2, 0.3)]
+    xs = np.concatenate([xs, np.asarray(extra_s, np.float32)])
+    xe = np.concatenate([xe, np.asarray(extra_e, np.float32)])
+    return xs, xe
+
+
+def bf_tof_bins(n):
+    rng = np.random.Generator(np.random.PCG64(12))
+    return rng.integers(-3, 4, size=n)
+
+
+# ---------------------------------------------------------------------------
+# hand-derived golden values
+# ---------------------------------------------------------------------------
+def test_hand_golden():
+    with open(os.path.join(GOLDEN, "hand_examples.json")) as f:
+        gold = json.load(f)
+    im = gold["image"]
+    g = G(im["shape"], im["origin"], im["voxsize"])
+    i0, i1, i2 = np.meshgrid(*[np.arange(n) for n in g.shape], indexing="ij")
+    img = 100.0 * i0 + 10.0 * i1 + i2
+    for case in gold["cases"]:
+        p = oracle.fwd([case["xs"]], [case["xe"]], img, g)[0]
+        assert p == pytest.approx(case["expected"], rel=1e-13, abs=1e-12), case["name"]
+
+
+# ---------------------------------------------------------------------------
+# brute force, three ways
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("mode", ["nontof", "tof_sino", "tof_lm"])
+def test_bruteforce_three_ways(mode):
+    xs, xe = bf_rays()
+    tof = None if mode == "nontof" else BF_TOF
+    tb = bf_tof_bins(len(xs)) if mode == "tof_lm" else None
+    A1 = dense_by_fwd(xs, xe, BF_GEOM, mode, tof, tb)
+    A2 = dense_by_back(xs, xe, BF_GEOM, mode, tof, tb)
+    A3 = dense_tent(xs, xe, BF_GEOM, mode, tof, tb)
+    scale = np.abs(A3).max()
+    assert scale > 0.1
+    assert np.abs(A1 - A2).max() <= 1e-14 * scale
+    assert np.abs(A1 - A3).max() <= 1e-13 * scale
+
+
+def test_principal_axis_ties():
+    assert oracle.principal_axis([0, 0, 0], [1, 1, 1]) == 0
+    assert oracle.principal_axis([0, 0, 0], [0.5, -1, 1]) == 1
+    assert oracle.principal_axis([0, 0, 0], [0.5, -1, 1.0000001]) == 2
+    # tie decided on the exact difference, not on a rounded one
+    xs = np.array([1e-9, 0.0, 0.0], np.float32)
+    xe = np.array([400.0, 400.0 - 1e-9 + 1e-9, 0.0], np.float32)
+    assert oracle.principal_axis(xs, xe) == _principal_axis_exact(xs, xe)
+    rng = np.random.Generator(np.random.PCG64(3))
+    for _ in range(200):
+        p = rng.normal(size=3).astype(np.float32) * 300
+        q = p.copy()
+        s = rng.normal() * 200
+        q[0] += np.float32(s)
+        q[1] = np.float32(p[1] + (q[0] - p[0]) * rng.choice([-1, 1]))
+        assert oracle.principal_axis(p, q) == _principal_axis_exact(p, q)
+
+
+# ---------------------------------------------------------------------------
+# adjoint identity <Ax, y> = <x, A^T y>
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("mode", ["nontof", "tof_sino", "tof_lm"])
+def test_adjoint(mode):
+    geom = G((13, 9, 11), (-7.1, -3.3, -6.0), (1.1, 1.7, 0.9))
+    sg = synth.ImageGeom(geom.shape, geom.origin, geom.voxsize)
+    xs1, xe1 = synth.random_lors(300, sg, seed=21)
+    xs2, xe2 = synth.random_lors(100, sg, seed=22, kind="inside")
+    xs, xe = np.concatenate([xs1, xs2]), np.concatenate([xe1, xe2])
+    tof = T(2.5, 2.0, 3.0, 11)
+    rng = np.random.Generator(np.random.PCG64(23))
+    tb = rng.integers(-5, 6, size=len(xs)) if mode == "tof_lm" else None
+    delta = rng.normal(size=len(xs)) if mode != "nontof" else None
+    x = rng.uniform(0, 1, size=geom.shape)
+    nout = tof.n_bins if mode == "tof_sino" else 1
+    y = rng.uniform(0, 1, size=(len(xs), nout)).reshape(-1)
+    Ax = oracle.fwd(xs, xe, x, geom, mode, tof if mode != "nontof" else None, tb, delta)
+    ATy = oracle.back(xs, xe, y, geom, mode, tof if mode != "nontof" else None, tb, delta)
+    lhs = float(np.dot(Ax.reshape(-1), y))
+    rhs = float(np.sum(x * ATy))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_threaded_equals_single():
+    g = synth.GEOM_SMALL
+    img = synth.ellipsoid_phantom(g, synth.PHANTOM_SMALL, 1001).numpy()
+    xs, xe = synth.random_lors(5000, g, seed=31)
+    p1 = oracle.fwd(xs, xe, img, g, threads=1)
+    p4 = oracle.fwd(xs, xe, img, g, threads=4)
+    assert np.array_equal(p1, p4)
+    y = synth.uniform_values(len(xs), 32)
+    b1 = oracle.back(xs, xe, y, g, threads=1)
+    b4 = oracle.back(xs, xe, y, g, threads=4)
+    assert np.abs(b1 - b4).max() <= 1e-12 * np.abs(b1).max()
+
+
+# ---------------------------------------------------------------------------
+# closed forms
+# ---------------------------------------------------------------------------
+def test_axis_aligned_voxel_sums():
+    geom = G((6, 5, 7), (-3.0, 10.0, -2.5), (1.2, 0.8, 2.0))
+    rng = np.random.Generator(np.random.PCG64(41))
+    img = rng.uniform(0, 5, size=geom.shape)
+    for a in range(3):
+        b, c = [i for i in range(3) if i != a]
+        for _ in range(5):
+            ib, ic = rng.integers(0, geom.shape[b]), rng.integers(0, geom.shape[c])
+            xs = np.zeros(3)
+            xs[b] = geom.origin[b] + ib * geom.voxsize[b]
+            xs[c] = geom.origin[c] + ic * geom.voxsize[c]
+            xe = xs.copy()
+            xs[a] = geom.origin[a] - 10.0
+            xe[a] = geom.origin[a] + geom.shape[a] * geom.voxsize[a] + 10.0
+            sl = [slice(None)] * 3
+            sl[b], sl[c] = ib, ic
+            expect = geom.voxsize[a] * img[tuple(sl)].sum()
+            p = oracle.fwd([xs], [xe], img, geom)[0]
+            assert p == pytest.approx(expect, rel=1e-13)
+            p_rev = oracle.fwd([xe], [xs], img, geom)[0]
+            assert p_rev == pytest.approx(expect, rel=1e-13)
+
+
+def test_affine_image_closed_form_and_uniform_cube():
+    """Affine image, every sample interior: bilinear interpolation is exact
+    and the plane sum is a midpoint rule, p = n_a v_a / cos_a * f(P_mid).
+    With f = 1 this is the chord length of the ray through the slab of
+    voxel edges, n_a v_a / cos_a (uniform cube)."""
+    geom = G((20, 20, 20), (-9.5, -9.5, -9.5), (1.0, 1.0, 1.0))
+    X, Y, Z = np.meshgrid(*[np.arange(20) * 1.0 - 9.5] * 3, indexing="ij")
+    alpha, beta = 2.0, np.array([0.3, -0.2, 0.15])
+    img = alpha + beta[0] * X + beta[1] * Y + beta[2] * Z
+    rng = np.random.Generator(np.random.PCG64(42))
+    for _ in range(40):
+        a = int(rng.integers(0, 3))
+        b, c = [i for i in range(3) if i != a]
+        d = np.zeros(3)
+        d[a] = 1.0
+        d[b], d[c] = rng.uniform(-0.3, 0.3, size=2)  # keeps samples interior
+        m = np.zeros(3)
+        m[b], m[c] = rng.uniform(-2, 2, size=2)
+        xs = m - 30 * d
+        xe = m + 30 * d
+        if rng.uniform() < 0.5:
+            xs, xe = xe, xs
+        cosa = 1.0 / np.linalg.norm(d)
+        Pmid = m  # the sample at the central plane (coordinate 0)
+        expect = 20 * 1.0 / cosa * (alpha + beta @ Pmid)
+        p = oracle.fwd([xs], [xe], img, geom)[0]
+        assert p == pytest.approx(expect, rel=1e-12)
+        pu = oracle.fwd([xs], [xe], np.ones(geom.shape), geom)[0]
+        assert pu == pytest.approx(20 * 1.0 / cosa, rel=1e-12)
+
+
+def test_parallel_rays_partition_of_unity():
+    """Back-projecting ones along a lattice of parallel rays offset by one
+    voxel pitch in (b, c) gives every interior voxel exactly v_a / cos_a."""
+    geom = G((8, 10, 9), (-4.0, -5.0, -4.0), (1.0, 1.25, 0.8))
+    for a, slopes in [(0, (0.31, -0.17)), (1, (-0.23, 0.41)), (2, (0.12, 0.27))]:
+        b, c = [i for i in range(3) if i != a]
+        d = np.zeros(3)
+        d[a] = 1.0
+        d[b], d[c] = slopes
+        xs_l, xe_l = [], []
+        for ib in range(-6, geom.shape[b] + 6):
+            for ic in range(-6, geom.shape[c] + 6):
+                p0 = np.zeros(3)
+                p0[a] = geom.origin[a]
+                p0[b] = geom.origin[b] + (ib + 0.37) * geom.voxsize[b]
+                p0[c] = geom.origin[c] + (ic + 0.61) * geom.voxsize[c]
+                xs_l.append(p0 - 40 * d)
+                xe_l.append(p0 + 40 * d)
+        img = oracle.back(xs_l, xe_l, np.ones(len(xs_l)), geom)
+        w0 = geom.voxsize[a] * np.linalg.norm(d) / 1.0
+        # the lattice spacing is one voxel pitch in b and c at every plane a
+        # only if the offsets are in voxel units at each plane: true because
+        # all rays are parallel and the lattice is defined on plane 0
+        interior = [slice(None)] * 3
+        interior[b] = slice(1, geom.shape[b] - 1)
+        interior[c] = slice(1, geom.shape[c] - 1)
+        vals = img[tuple(interior)]
+        assert np.allclose(vals, w0, rtol=1e-12, atol=0)
+
+
+# ---------------------------------------------------------------------------
+# TOF
+# ---------------------------------------------------------------------------
+def test_tof_weight_vs_quadrature():
+    """g = integral over the bin [c - D/2, c + D/2] of the Gaussian pdf of
+    width sigma centred on tau (composite Simpson, 4000 panels)."""
+    D, s = 28.0, 24.503
+    for tau, cen in [(0.0, 0.0), (13.0, 28.0), (-40.0, 28.0), (70.0, 0.0), (-50.0, -28.0)]:
+        x = np.linspace(cen - D / 2, cen + D / 2, 8001)
+        pdf = np.exp(-0.5 * ((x - tau) / s) ** 2) / (s * math.sqrt(2 * math.pi))
+        h = x[1] - x[0]
+        simpson = h / 3 * (pdf[0] + pdf[-1] + 4 * pdf[1:-1:2].sum() + 2 * pdf[2:-1:2].sum())
+        assert oracle.tof_weight(tau, cen, D, s, 3.0) == pytest.approx(simpson, rel=1e-12)
+    # truncation: zero beyond n_sigmas*sigma + D/2
+    assert oracle.tof_weight(3 * s + D / 2 + 1e-6, 0.0, D, s, 3.0) == 0.0
+    assert oracle.tof_weight(3 * s + D / 2 - 1e-6, 0.0, D, s, 3.0) > 0.0
+
+
+def _line_geom():
+    return G((40, 3, 3), (-39.0, -2.0, -2.0), (2.0, 2.0, 2.0))
+
+
+def test_tof_sum_equals_nontof():
+    geom = G((30, 20, 10), (-29.0, -19.0, -9.0), (2.0, 2.0, 2.0))
+    sg = synth.ImageGeom(geom.shape, geom.origin, geom.voxsize)
+    rng = np.random.Generator(np.random.PCG64(51))
+    img = rng.uniform(0, 2, size=geom.shape)
+    xs, xe = synth.random_lors(200, sg, seed=52)
+    p = oracle.fwd(xs, xe, img, geom)
+    # window covers every ray (N*D >= L + 2 n_sigmas sigma + D) with n_sigmas = 8
+    tof8 = T(10.0, 4.0, 8.0, 41)
+    pt = oracle.fwd(xs, xe, img, geom, "tof_sino", tof8)
+    assert np.allclose(pt.sum(1), p, rtol=1e-12, atol=1e-12 * p.max())
+    # n_sigmas = 3: telescoping bound sum_t g_t in [erf(3/sqrt2), 1] per sample
+    tof3 = T(10.0, 4.0, 3.0, 41)
+    pt3 = oracle.fwd(xs, xe, img, geom, "tof_sino", tof3)
+    lo = math.erf(3 / math.sqrt(2))
+    assert np.all(pt3.sum(1) >= lo * p - 1e-12 * p.max())
+    assert np.all(pt3.sum(1) <= p + 1e-12 * p.max())
+
+
+def test_mirror_symmetry():
+    geom = G((16, 12, 10), (-15.0, -11.0, -9.0), (2.0, 2.0, 2.0))
+    sg = synth.ImageGeom(geom.shape, geom.origin, geom.voxsize)
+    rng = np.random.Generator(np.random.PCG64(61))
+    img = rng.uniform(0, 2, size=geom.shape)
+    xs, xe = synth.random_lors(300, sg, seed=62)
+    tof = T(7.0, 5.0, 3.0, 9)
+    assert np.allclose(oracle.fwd(xs, xe, img, geom), oracle.fwd(xe, xs, img, geom), rtol=1e-12)
+    a = oracle.fwd(xs, xe, img, geom, "tof_sino", tof)
+    b = oracle.fwd(xe, xs, img, geom, "tof_sino", tof)
+    assert np.allclose(a, b[:, ::-1], rtol=1e-12, atol=1e-13 * np.abs(a).max())
+    tb = rng.integers(-4, 5, size=len(xs))
+    la = oracle.fwd(xs, xe, img, geom, "tof_lm", tof, tof_bin=tb)
+    lb = oracle.fwd(xe, xs, img, geom, "tof_lm", tof, tof_bin=-tb)
+    assert np.allclose(la, lb, rtol=1e-12, atol=1e-13 * np.abs(la).max())
+    # the sign convention itself: bins increase toward xe
+    line = _line_geom()
+    one = np.zeros(line.shape)
+    one[35, 1, 1] = 1.0  # a hot voxel near the xe end
+    pt = oracle.fwd([(-100.0, 0.0, 0.0)], [(100.0, 0.0, 0.0)], one, line, "tof_sino",
+                    T(10.0, 3.0, 3.0, 21))[0]
+    assert int(np.argmax(pt)) > 10
+
+
+def test_lm_equals_sino():
+    geom = G((16, 12, 10), (-15.0, -11.0, -9.0), (2.0, 2.0, 2.0))
+    sg = synth.ImageGeom(geom.shape, geom.origin, geom.voxsize)
+    rng = np.random.Generator(np.random.PCG64(71))
+    img = rng.uniform(0, 2, size=geom.shape)
+    xs, xe = synth.random_lors(300, sg, seed=72)
+    tof = T(7.0, 5.0, 3.0, 9)
+    delta = rng.normal(size=len(xs)) * 3
+    ps = oracle.fwd(xs, xe, img, geom, "tof_sino", tof, delta=delta)
+    for ts in range(-4, 5):
+        pl = oracle.fwd(xs, xe, img, geom, "tof_lm", tof, tof_bin=np.full(len(xs), ts), delta=delta)
+        assert np.array_equal(pl, ps[:, ts + 4])
+    tbv = rng.integers(-4, 5, size=len(xs))
+    y = rng.uniform(size=len(xs))
+    ysino = np.zeros((len(xs), 9))
+    ysino[np.arange(len(xs)), tbv + 4] = y
+    bl = oracle.back(xs, xe, y, geom, "tof_lm", tof, tof_bin=tbv, delta=delta)
+    bs = oracle.back(xs, xe, ysino, geom, "tof_sino", tof, delta=delta)
+    assert np.allclose(bl, bs, rtol=1e-12, atol=1e-13 * np.abs(bl).max())
+
+
+def test_translation_invariance():
+    geom = G((12, 10, 8), (-11.0, -9.0, -7.0), (2.0, 1.5, 1.0))
+    sg = synth.ImageGeom(geom.shape, geom.origin, geom.voxsize)
+    rng = np.random.Generator(np.random.PCG64(81))
+    img = rng.uniform(0, 2, size=geom.shape)
+    xs, xe = synth.random_lors(200, sg, seed=82)
+    shift = np.array([3 * 2.0, -2 * 1.5, 5 * 1.0])
+    g2 = G(geom.shape, tuple(np.array(geom.origin) + shift), geom.voxsize)
+    tof = T(6.0, 4.0, 3.0, 7)
+    for mode in ["nontof", "tof_sino"]:
+        t = tof if mode != "nontof" else None
+        a = oracle.fwd(xs, xe, img, geom, mode, t)
+        b = oracle.fwd(xs.astype(np.float64) + shift, xe.astype(np.float64) + shift, img, g2, mode, t)
+        assert np.allclose(a, b, rtol=1e-10, atol=1e-11 * np.abs(a).max())
+
+
+# ---------------------------------------------------------------------------
+# OSEM and gradient
+# ---------------------------------------------------------------------------
+def _small_lm_problem(n_events=3000, seed=91):
+    g = synth.ImageGeom.centred((16, 16, 8), (2.0, 2.0, 2.0))
+    ph = synth.PhantomSpec((12.0, 10.0, 6.0), (3.0,))
+    x = synth.ellipsoid_phantom(g, ph, seed).numpy()
+    tof = synth.TOF_CLINICAL
+    xs, xe, tb = synth.lm_events(synth.ellipsoid_phantom(g, ph, seed), g, synth.SCANNER_CLINICAL,
+                                 tof, n_events, seed)
+    return g, tof, x, xs.numpy(), xe.numpy(), tb.numpy()
+
+
+def test_osem_count_preservation():
+    """sum_j (s_j / n_sub) x_new_j = sum_{e in S} (Ax)_e / ((Ax)_e + b), for
+    any sensitivity s > 0 (here a random positive image)."""
+    g, tof, x, xs, xe, tb = _small_lm_problem()
+    rng = np.random.Generator(np.random.PCG64(92))
+    sens = rng.uniform(0.5, 2.0, size=g.shape)
+    b, n_sub, m = 0.7, 4, 1
+    x0 = rng.uniform(0.2, 1.5, size=g.shape)
+    x1 = oracle.lm_osem_subset_update(x0, xs, xe, tb, g, tof, sens, b, m, n_sub)
+    p = oracle.fwd(xs[m::n_sub], xe[m::n_sub], x0, g, "tof_lm", tof, tof_bin=tb[m::n_sub])
+    lhs = float(np.sum(sens / n_sub * x1))
+    rhs = float(np.sum(p / (p + b)))
+    assert lhs == pytest.approx(rhs, rel=1e-12)
+    assert np.all(x1 >= 0)
+    # b = 0: the preserved count is the subset size (events with Ax > 0)
+    x1b = oracle.lm_osem_subset_update(x0, xs, xe, tb, g, tof, sens, 0.0, m, n_sub)
+    assert float(np.sum(sens / n_sub * x1b)) == pytest.approx(float(np.sum(p > 0)), rel=1e-12)
+
+
+def test_gradient_vs_finite_differences():
+    g, tof, x, xs, xe, tb = _small_lm_problem(n_events=2000, seed=93)
+    rng = np.random.Generator(np.random.PCG64(94))
+    w = rng.uniform(0.5, 1.5, size=len(xs))
+    b = 0.3
+    x = x + 0.1
+    f0, grad = oracle.poisson_loglik_grad(x, xs, xe, tb, g, tof, w, b)
+    h = 1e-6
+    idx = rng.choice(x.size, size=40, replace=False)
+    for j in idx:
+        e = np.zeros(x.size)
+        e[j] = h
+        e = e.reshape(x.shape)
+        # f(x+h e_j) - f(x-h e_j), summed per event as log1p of the relative
+        # change so that the O(|f|) rounding of the full sums does not swamp
+        # the O(h) difference
+        pp = oracle.fwd(xs, xe, x + e, g, "tof_lm", tof, tof_bin=tb)
+        pm = oracle.fwd(xs, xe, x - e, g, "tof_lm", tof, tof_bin=tb)
+        fd = float(np.sum(w * np.log1p((pp - pm) / (pm + b)))) / (2 * h)
+        gj = grad.reshape(-1)[j]
+        assert abs(fd - gj) <= 1e-7 * max(abs(gj), 1e-3 * np.abs(grad).max()), (j, fd, gj)
+
+
+# ---------------------------------------------------------------------------
+# planted mistakes must be caught
+# ---------------------------------------------------------------------------
+def _pins(mutant):
+    """Fast versions of the pins above, run against a (possibly mutated)
+    oracle build.  Returns the names of the pins that failed."""
+    failed = []
+    xs, xe = bf_rays()
+    for mode in ["nontof", "tof_sino", "tof_lm"]:
+        tof = None if mode == "nontof" else BF_TOF
+        tb = bf_tof_bins(len(xs)) if mode == "tof_lm" else None
+        A1 = dense_by_fwd(xs, xe, BF_GEOM, mode, tof, tb, mutant=mutant)
+        A3 = dense_tent(xs, xe, BF_GEOM, mode, tof, tb)
+        if np.abs(A1 - A3).max() > 1e-13 * np.abs(A3).max():
+            failed.append("bruteforce-" + mode)
+    D, s = 28.0, 24.503
+    x = np.linspace(-D / 2, D / 2, 8001)
+    pdf = np.exp(-0.5 * ((x - 5.0) / s) ** 2) / (s * math.sqrt(2 * math.pi))
+    h = x[1] - x[0]
+    simpson = h / 3 * (pdf[0] + pdf[-1] + 4 * pdf[1:-1:2].sum() + 2 * pdf[2:-1:2].sum())
+    if abs(oracle.tof_weight(5.0, 0.0, D, s, 3.0, mutant=mutant) - simpson) > 1e-12 * simpson:
+        failed.append("quadrature")
+    with open(os.path.join(GOLDEN, "hand_examples.json")) as f:
+        gold = json.load(f)
+    im = gold["image"]
+    gg = G(im["shape"], im["origin"], im["voxsize"])
+    i0, i1, i2 = np.meshgrid(*[np.arange(n) for n in gg.shape], indexing="ij")
+    himg = 100.0 * i0 + 10.0 * i1 + i2
+    for case in gold["cases"]:
+        p = oracle.fwd([case["xs"]], [case["xe"]], himg, gg, mutant=mutant)[0]
+        if abs(p - case["expected"]) > 1e-12 * max(1.0, abs(case["expected"])):
+            failed.append("golden")
+            break
+    geom = G((20, 20, 20), (-9.5, -9.5, -9.5), (1.0, 1.0, 1.0))
+    pu = oracle.fwd([(-30.0, -3.0, 1.0)], [(30.0, 4.0, -2.0)], np.ones(geom.shape), geom,
+                    mutant=mutant)[0]
+    if abs(pu - 20 * math.sqrt(60 ** 2 + 7 ** 2 + 3 ** 2) / 60) > 1e-12 * pu:
+        failed.append("uniform-cube")
+    return failed
+
+
+def test_planted_mistakes_are_caught():
+    assert _pins(0) == []
+    for mutant in range(1, 8):
+        oracle.joseph.build(mutant)
+        assert _pins(mutant), f"planted mistake {mutant} not caught"
