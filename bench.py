@@ -1,0 +1,407 @@
+"""Benchmark: TOF listmode Joseph forward + back projection, events/s.
+
+Workload (default): 8 images of 200x200x71 voxels (2 mm), 40M synthetic TOF
+listmode events each (320M events), clinical scanner (36 rings x 672
+crystals, R = 400 mm), 29 TOF bins of 28 mm, FWHM 57.7 mm, 3 sigma.  One
+step = sort/pack all events into the plan (binning) + forward projection of
+the batch through the autograd Function + the loss sum(w log(Ax + b)) + its
+backward (the adjoint kernel).  events/s = events in the batch / step time.
+
+Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Under torchrun each rank runs its own batch (weak scaling, no collective on
+the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_FRAMES = 8
+EVENTS_PER_FRAME = 40_000_000
+METRIC = "TOF listmode fwd+back events/s"
+UNIT = "events/s"
+
+
+# ---------------------------------------------------------------------------
+# environment helpers
+# ---------------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks/throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+def make_tof_lm_batch(rank: int, n_frames: int, events: int, device):
+    from paper_2212_12519_gb300 import synth
+    g = synth.GEOM_CLINICAL
+    tof = synth.TOF_CLINICAL
+    imgs, xs_l, xe_l, tb_l, bvals = [], [], [], [], []
+    for f in range(n_frames):
+        seed = 4001 + f + 1000 * 100 * rank
+        ph = synth.ellipsoid_phantom(g, synth.PHANTOM_CLINICAL, seed, device=device)
+        xs, xe, tb = synth.lm_events(ph, g, synth.SCANNER_CLINICAL, tof, events, seed=seed + 50,
+                                     device=device)
+        imgs.append(ph)
+        xs_l.append(xs)
+        xe_l.append(xe)
+        tb_l.append(tb)
+        bvals.append(synth.background_level(ph, tof))
+    xs = torch.cat(xs_l)
+    xe = torch.cat(xe_l)
+    tb = torch.cat(tb_l)
+    del xs_l, xe_l, tb_l
+    w = synth.loss_weights(xs.shape[0], 4999 + rank, device=device)
+    offsets = [events * f for f in range(n_frames + 1)]
+    bvec = torch.repeat_interleave(torch.tensor(bvals, dtype=torch.float32, device=device),
+                                   torch.full((n_frames,), events, device=device))
+    x = torch.stack(imgs).contiguous()
+    return dict(geom=g, tof=tof, xs=xs.contiguous(), xe=xe.contiguous(), tb=tb.contiguous(),
+                w=w, bvec=bvec.contiguous(), x=x, offsets=offsets, bvals=bvals)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch.distributed as dist
+    from paper_2212_12519_gb300 import ops
+    from paper_2212_12519_gb300.autograd import JosephTOFLM
+    from paper_2212_12519_gb300 import build as jbuild
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    jbuild.build()
+    ops.load()
+    n_frames, epf = args.frames, args.events
+    W = make_tof_lm_batch(rank, n_frames, epf, dev)
+    g, tof = W["geom"], W["tof"]
+    n_total = W["xs"].shape[0]
+    plan = ops.jp_plan_create_batch(W["xs"], W["xe"], g, W["offsets"], tof_bin=W["tb"],
+                                    tof_bin_width=tof.bin_width)
+    x = W["x"].clone().requires_grad_(True)
+    stream = torch.cuda.current_stream()
+
+    timers = {"fwd": [], "back": [], "bin": []}
+
+    def timed(name, fn):
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        r = fn()
+        e.record(stream)
+        timers[name].append((s, e))
+        return r
+
+    class TimedTOFLM(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, xx):
+            ctx.shape = xx.shape
+            return timed("fwd", lambda: ops.jp_fwd_tof_lm(plan, xx.contiguous(), tof))
+
+        @staticmethod
+        def backward(ctx, gp):
+            gx = torch.zeros(ctx.shape, dtype=torch.float32, device=gp.device)
+            timed("back", lambda: ops.jp_back_tof_lm(plan, gp.contiguous(), tof, gx))
+            return gx
+
+    def step(record=True):
+        if record:
+            timed("bin", lambda: ops.jp_plan_rebind(plan, W["xs"], W["xe"], W["offsets"], tof_bin=W["tb"]))
+        else:
+            ops.jp_plan_rebind(plan, W["xs"], W["xe"], W["offsets"], tof_bin=W["tb"])
+        x.grad = None
+        p = TimedTOFLM.apply(x) if record else JosephTOFLM.apply(x, plan, tof)
+        loss = (W["w"] * torch.log(p + W["bvec"])).sum()
+        loss.backward()
+        return loss
+
+    for _ in range(args.warmup):
+        step(record=False)
+    torch.cuda.synchronize()
+    for k in timers:
+        timers[k].clear()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = ops.jp_launch_count()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        loss = step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    launches = ops.jp_launch_count() - launches0
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1) / args.steps
+    if ws > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    kern = {k: statistics.mean(s.elapsed_time(e) for s, e in v) for k, v in timers.items() if v}
+
+    # exact algorithmic work of one TOF-LM launch
+    samples = ops.jp_count_samples(plan, "tof_lm", tof)
+    value = n_total * ws / (ms / 1e3)
+
+    # ---- e2e through the public API with host buffers --------------------
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, W, plan, g, tof, dev, ws)
+
+    if rank == 0:
+        peaks, peak_kind = measured_peaks()
+        # dominant kernel: the back projection (scatter), reported against HBM
+        dom = "back" if kern.get("back", 0) >= kern.get("fwd", 0) else "fwd"
+        nvox = int(np.prod(g.shape))
+        alg_bytes = n_total * (24 + 2 + 4) + n_frames * nvox * 4 * (2 if dom == "back" else 1)
+        achieved = alg_bytes / (kern[dom] / 1e3) / 1e9
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"tof_lm_batch{n_frames}x{epf // 1_000_000}M_200x200x71",
+                       "frames_per_gpu": n_frames, "events_per_frame": epf, "image": list(g.shape),
+                       "tof_bins": tof.n_bins, "l2": "inputs (>10 GB/step) larger than L2, no flush",
+                       "parallelism": f"dp{ws} (independent batches)"},
+            "kernel_ms": kern,
+            "samples_per_step": samples,
+            "events_per_s_excl_binning": n_total * ws / ((ms - kern.get("bin", 0.0)) / 1e3),
+            "roofline": {"bound": "hbm", "kernel": f"{dom}_tof_lm", "achieved": achieved,
+                         "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                         "traffic": None, "peak_source": peak_kind,
+                         "alg_bytes_per_launch": alg_bytes},
+            "clocks": clk,
+            "gpu_launches": int(launches),
+            "e2e": e2e,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(W, g, tof, target_s=args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def run_e2e(args, W, plan, g, tof, dev, ws):
+    """Same step through the public API, inputs from pinned host memory and
+    the loss + gradient images read back every step."""
+    from paper_2212_12519_gb300 import ops
+    from paper_2212_12519_gb300.autograd import JosephTOFLM
+    host = {k: W[k].cpu().pin_memory() for k in ("xs", "xe", "tb", "w", "bvec", "x")}
+    dbuf = {k: torch.empty_like(W[k]) for k in host}
+    out_grad = torch.empty(W["x"].shape, dtype=torch.float32).pin_memory()
+    out_loss = torch.empty((), dtype=torch.float32).pin_memory()
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    d2h = out_grad.numel() * 4 + 4
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for k in host:
+            dbuf[k].copy_(host[k], non_blocking=True)
+        ops.jp_plan_rebind(plan, dbuf["xs"], dbuf["xe"], W["offsets"], tof_bin=dbuf["tb"])
+        x = dbuf["x"].requires_grad_(True)
+        p = JosephTOFLM.apply(x, plan, tof)
+        loss = (dbuf["w"] * torch.log(p + dbuf["bvec"])).sum()
+        loss.backward()
+        out_grad.copy_(x.grad, non_blocking=True)
+        out_loss.copy_(loss.detach(), non_blocking=True)
+        x.grad = None
+        dbuf["x"] = dbuf["x"].detach()
+
+    for _ in range(max(1, min(args.warmup, 2))):
+        step()
+    torch.cuda.synchronize()
+    n = max(2, args.steps // 2)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(n):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / n
+    return {"value": W["xs"].shape[0] * ws / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+            "steps": n, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline / reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+def _oracle_events(W, n):
+    xs = W["xs"][:n].cpu().numpy()
+    xe = W["xe"][:n].cpu().numpy()
+    tb = W["tb"][:n].cpu().numpy()
+    img = W["x"][0].detach().cpu().numpy()
+    w = W["w"][:n].cpu().numpy()
+    return xs, xe, tb, img, w
+
+
+def oracle_step(xs, xe, tb, img, w, g, tof, b, threads):
+    import oracle
+    p = oracle.fwd(xs, xe, img, g, "tof_lm", tof, tof_bin=tb, threads=threads)
+    q = w / (p + b)
+    oracle.back(xs, xe, q, g, "tof_lm", tof, tof_bin=tb, threads=threads)
+
+
+def cpu_baseline(W, g, tof, target_s=12.0):
+    import oracle
+    oracle.build()
+    threads = os.cpu_count() or 1
+    n0 = 100_000
+    xs, xe, tb, img, w = _oracle_events(W, n0)
+    t = time.perf_counter()
+    oracle_step(xs, xe, tb, img, w, g, tof, W["bvals"][0], threads)
+    dt = time.perf_counter() - t
+    n = int(min(W["xs"].shape[0], max(n0, n0 * target_s / max(dt, 1e-3))))
+    xs, xe, tb, img, w = _oracle_events(W, n)
+    t = time.perf_counter()
+    oracle_step(xs, xe, tb, img, w, g, tof, W["bvals"][0], threads)
+    dt = time.perf_counter() - t
+    return {"value": n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"first {n} events of frame 0 (of {W['xs'].shape[0]}), FP64 fwd+back, {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    from paper_2212_12519_gb300 import synth
+    dev = "cpu"
+    # a bounded sample of the same workload, generated on the host
+    g = synth.GEOM_CLINICAL
+    tof = synth.TOF_CLINICAL
+    ph = synth.ellipsoid_phantom(g, synth.PHANTOM_CLINICAL, 4001, device=dev)
+    n = args.ref_events
+    xs, xe, tb = synth.lm_events(ph, g, synth.SCANNER_CLINICAL, tof, n, seed=4051, device=dev)
+    w = synth.loss_weights(n, 4999, device=dev)
+    b = synth.background_level(ph, tof)
+    import oracle
+    oracle.build()
+    threads = os.cpu_count() or 1
+    a = (xs.numpy(), xe.numpy(), tb.numpy(), ph.numpy(), w.numpy())
+    for _ in range(args.warmup):
+        oracle_step(*a, g, tof, b, threads)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_step(*a, g, tof, b, threads)
+    dt = (time.perf_counter() - t) / args.steps
+    value = n / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"tof_lm_batch{N_FRAMES}x{EVENTS_PER_FRAME // 1_000_000}M_200x200x71",
+                       "sample": f"{n} events of frame 0 per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{n} events per step, FP64 fwd+back"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--frames", type=int, default=N_FRAMES)
+    ap.add_argument("--events", type=int, default=EVENTS_PER_FRAME)
+    ap.add_argument("--ref-events", type=int, default=400_000)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

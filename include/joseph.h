@@ -1,0 +1,216 @@
+/*
+ * joseph.h -- C ABI of libjoseph, a GB300 (sm_103a) Joseph projector.
+ *
+ * The library computes Joseph's ray-driven forward projection and its exact
+ * adjoint (back projection) of a 3D voxel image along lines of response
+ * (LORs) given by their start and end points (paper Sec. 2.1, Fig. 1; the
+ * generic "list of start and end points" interface of Sec. 2.2), in three
+ * forms (Sec. 2.2): non-TOF, TOF sinogram (all TOF bins of a LOR in one
+ * traversal) and TOF listmode (the single TOF bin of each event).  The TOF
+ * kernel is a Gaussian of width sigma integrated over a TOF bin, i.e. a
+ * difference of two error functions, truncated at n_sigmas (Sec. 2.1, 2.6).
+ *
+ * Conventions (the same for every call):
+ *   image     float32, C order [n0][n1][n2] (axis 2 fastest); `origin` is the
+ *             world coordinate (mm) of the CENTRE of voxel (0,0,0); voxel
+ *             sizes may differ per axis.
+ *   LOR       start xs and end xe, float32 [n][3] (mm).  The principal axis
+ *             a = argmax_i |xe_i - xs_i| (lowest index on exact ties) is
+ *             decided exactly; every plane k of axis a whose centre
+ *             o_a + k v_a lies in [min(xs_a,xe_a), max(xs_a,xe_a)] contributes
+ *             a bilinear interpolation of the 4 nearest voxels (zero outside
+ *             the grid); the sum is scaled by v_a / cos_a.  xs == xe projects
+ *             to 0; a LOR missing the image projects to 0.
+ *   TOF       tau = signed distance of a plane sample from the LOR midpoint,
+ *             positive toward xe.  Sinogram bin t of N has centre
+ *             (t - (N-1)/2) * bin_width + delta; a listmode event with signed
+ *             bin t_s has centre t_s * bin_width + delta (delta = optional
+ *             per-LOR TOF centre offset, default 0).  Weight
+ *             g = 1/2 [erf((tau-c+w/2)/(sqrt2 s)) - erf((tau-c-w/2)/(sqrt2 s))]
+ *             if |tau - c| <= n_sigmas*s + w/2, else 0.  TOF sinograms are
+ *             float32 [n_lor][N] (TOF fastest).
+ *   pointers  every array argument is a DEVICE pointer owned by the caller
+ *             (the library never frees it) unless stated otherwise; `stream`
+ *             is a cudaStream_t (NULL = legacy default stream).  All
+ *             projection calls are asynchronous on `stream` and allocate
+ *             nothing.  Forward calls overwrite their output; back
+ *             projections ACCUMULATE into the image (the caller zeroes it).
+ *   errors    every call returns JP_OK (0) or a negative JP_ERR_* code;
+ *             jp_last_error() gives a message for the calling thread.
+ *             Argument checks run on the host before anything is launched.
+ *   threads   distinct plans may be used from distinct host threads; one plan
+ *             must not be rebound while a call using it is in flight, and two
+ *             back projections into the same image must not overlap on
+ *             different streams.
+ */
+#ifndef JOSEPH_H
+#define JOSEPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define JP_OK 0
+#define JP_ERR_ARG (-1)     /* null pointer, size <= 0, non-finite or non-positive parameter */
+#define JP_ERR_ALIGN (-2)   /* pointer not aligned to its element type */
+#define JP_ERR_CUDA (-3)    /* CUDA runtime error (message in jp_last_error) */
+#define JP_ERR_TIMEOUT (-4) /* a bounded device-side wait gave up */
+#define JP_ERR_NOMEM (-5)   /* device allocation failed (plan creation only) */
+#define JP_ERR_STATE (-6)   /* plan lacks what the call needs (e.g. TOF bins) */
+
+#define JP_MAX_TOF_BINS 128
+
+typedef struct jp_plan_s* jp_plan;
+
+/* image grid: shape, centre of voxel (0,0,0) in mm, voxel size in mm */
+typedef struct {
+  int32_t n[3];
+  float origin[3];
+  float voxsize[3];
+} jp_image_geom;
+
+/* TOF kernel: bin width (mm), Gaussian sigma (mm, = FWHM / 2.35482),
+ * truncation in sigmas, number of sinogram TOF bins (unused in listmode). */
+typedef struct {
+  float bin_width;
+  float sigma;
+  float n_sigmas;
+  int32_t n_bins;
+} jp_tof;
+
+/* Plan options (zero-initialise for defaults).  A plan sorts its LORs into
+ * bins by principal axis, in-plane direction and position so that the 32
+ * LORs of a warp walk nearly the same voxels (paper Sec. 4 suggests event
+ * pre-sorting; Sec. 2.6 and 3 show the memory-order sensitivity it removes). */
+typedef struct {
+  int32_t block;          /* threads per CTA for projections (0 = 256; 64..1024, multiple of 32) */
+  int32_t slope_bins;     /* bins over the in-plane slope d_b/d_a in [-1,1] (0 = 64) */
+  int32_t offset_bins;    /* bins over the in-plane offset at the central plane (0 = 64) */
+  int32_t window_bins;    /* bins over the TOF-window centre along the principal
+                             axis, listmode plans only (0 = 16) */
+  float tof_bin_width;    /* mm; > 0 with tof_bin given: bin listmode events by
+                             their TOF window centre; 0 = ignore */
+  int32_t flags;          /* JP_PLAN_KEEP_ORDER: no sorting (identity order) */
+} jp_plan_opts;
+
+#define JP_PLAN_KEEP_ORDER 1
+
+/*
+ * jp_plan_create_batch -- sort and pack the LORs of n_frames frames.
+ *   xstart, xend       device float32 [n_total][3] (mm), caller order
+ *   tof_bin            device int16 [n_total] signed listmode TOF bins, or NULL
+ *   tof_center_offset  device float32 [n_total] TOF centre offsets delta (mm), or NULL
+ *   frame_offsets      HOST int64 [n_frames+1], frame f owns LORs
+ *                      [frame_offsets[f], frame_offsets[f+1]); offsets[0] = 0,
+ *                      non-decreasing; n_total = offsets[n_frames] < 2^31
+ *   g, opts            image grid (all frames share it); opts may be NULL
+ * The plan allocates device memory for exactly n_total LORs and n_frames
+ * frames (its capacity) and copies what it needs: the input arrays may be
+ * freed once the stream has passed this call.  Frame f of a batched call
+ * reads/writes image f at `image + f * img_stride`.
+ * Errors: JP_ERR_ARG, JP_ERR_ALIGN, JP_ERR_NOMEM, JP_ERR_CUDA.
+ */
+int jp_plan_create_batch(jp_plan* out, const float* xstart, const float* xend,
+                         const int16_t* tof_bin, const float* tof_center_offset,
+                         const int64_t* frame_offsets, int32_t n_frames,
+                         const jp_image_geom* g, const jp_plan_opts* opts, void* stream);
+
+/* single-frame form: frame_offsets = {0, n_lor} */
+int jp_plan_create(jp_plan* out, const float* xstart, const float* xend,
+                   const int16_t* tof_bin, const float* tof_center_offset, int64_t n_lor,
+                   const jp_image_geom* g, const jp_plan_opts* opts, void* stream);
+
+/*
+ * jp_plan_rebind -- re-sort new LORs into an existing plan without allocating
+ * (same arguments as jp_plan_create_batch; n_total and n_frames must not
+ * exceed the plan's capacity).  Asynchronous on `stream`.
+ */
+int jp_plan_rebind(jp_plan p, const float* xstart, const float* xend, const int16_t* tof_bin,
+                   const float* tof_center_offset, const int64_t* frame_offsets,
+                   int32_t n_frames, void* stream);
+
+/* releases the plan's device memory (synchronises the device first) */
+int jp_plan_destroy(jp_plan p);
+
+/* number of LORs / frames currently bound (host pointers, may be NULL);
+ * perm_out (device int32 [n_lor] or NULL) receives a copy of the plan's
+ * permutation, binned position -> caller index, asynchronously on stream */
+int jp_plan_info(jp_plan p, int64_t* n_lor, int32_t* n_frames, int32_t* perm_out, void* stream);
+
+/*
+ * Planned projections.  img / img_accum: device float32 images, frame f at
+ * offset f*img_stride elements (img_stride = 0: every frame uses the same
+ * image).  proj: caller order, float32 [n_total] or [n_total][N] (TOF sino).
+ * TOF listmode calls need a plan created with tof_bin; delta comes from the
+ * plan (0 if it was created without tof_center_offset).
+ */
+int jp_fwd(jp_plan p, const float* img, int64_t img_stride, float* proj, void* stream);
+int jp_back(jp_plan p, const float* proj, float* img_accum, int64_t img_stride, void* stream);
+int jp_fwd_tof_sino(jp_plan p, const float* img, int64_t img_stride, const jp_tof* t,
+                    float* proj, void* stream);
+int jp_back_tof_sino(jp_plan p, const float* proj, const jp_tof* t, float* img_accum,
+                     int64_t img_stride, void* stream);
+int jp_fwd_tof_lm(jp_plan p, const float* img, int64_t img_stride, const jp_tof* t,
+                  float* proj, void* stream);
+int jp_back_tof_lm(jp_plan p, const float* proj, const jp_tof* t, float* img_accum,
+                   int64_t img_stride, void* stream);
+
+/*
+ * Planless projections: one thread per LOR in caller order, reading the
+ * endpoint arrays directly (the paper's own parallelisation, Sec. 2.2).
+ *   tof_mode  0 non-TOF, 1 TOF sinogram, 2 TOF listmode
+ *   t         TOF parameters (NULL for tof_mode 0)
+ *   tof_bin   int16 [n] (tof_mode 2), else ignored; tof_center_offset may be NULL
+ * Same output conventions as the planned calls.  Allocates nothing.
+ */
+int jp_fwd_lors(const float* xstart, const float* xend, const int16_t* tof_bin,
+                const float* tof_center_offset, int64_t n_lor, const jp_image_geom* g,
+                int32_t tof_mode, const jp_tof* t, const float* img, float* proj, void* stream);
+int jp_back_lors(const float* xstart, const float* xend, const int16_t* tof_bin,
+                 const float* tof_center_offset, int64_t n_lor, const jp_image_geom* g,
+                 int32_t tof_mode, const jp_tof* t, const float* proj, float* img_accum,
+                 void* stream);
+
+/*
+ * Listmode OSEM element-wise steps (paper Sec. 2.6 and 3, listmode OSEM:
+ * x <- x / s_sub * A_S^T (1 / (A_S x + b))).
+ *   jp_osem_ratio   q[e] = 1 / (p[e] + b[frame(e)])   (q may alias p)
+ *                   b: device float32 [n_frames]; frame of e from the plan's
+ *                   frame offsets (plan may be NULL: one frame, b[0])
+ *   jp_osem_update  x[f][j] = s[f][j] > 0 ? x[f][j] * bp[f][j] / (s[f][j]*scale) : 0
+ *                   for n_frames images of nvox voxels, strides img_stride
+ *                   (x, bp, s); s_stride = 0 shares one sensitivity image.
+ * Errors: JP_ERR_ARG, JP_ERR_ALIGN, JP_ERR_CUDA.
+ */
+int jp_osem_ratio(jp_plan p, const float* proj, const float* b, float* q, int64_t n,
+                  void* stream);
+int jp_osem_update(float* x, const float* bp, const float* sens, float scale, int64_t nvox,
+                   int32_t n_frames, int64_t img_stride, int64_t s_stride, void* stream);
+
+/* FP64 sum of a float32 device array into *out (device double).  Used only
+ * for the sensitivity-normalisation check sum_j (A^T 1)_j = sum_i (A 1)_i. */
+int jp_sum_f64(const float* x, int64_t n, double* out, void* stream);
+
+/* Number of plane samples the projector visits for the plan's LORs in the
+ * given mode (0 non-TOF, 2 TOF listmode; TOF sinograms visit the non-TOF
+ * planes), summed into *out (device uint64, overwritten).  Used to state
+ * the algorithmic work of a launch (samples x bytes or flops per sample). */
+int jp_count_samples(jp_plan p, int32_t tof_mode, const jp_tof* t, uint64_t* out, void* stream);
+
+/* total number of kernels this library has launched in the process */
+uint64_t jp_launch_count(void);
+
+/* thread-local message of the last failing call ("" if none) */
+const char* jp_last_error(void);
+
+/* library version string */
+const char* jp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JOSEPH_H */

@@ -1,0 +1,122 @@
+// Listmode OSEM element-wise kernels (step a8; paper Sec. 2.6 and 3:
+// x <- x / s_sub * A_S^T (1 / (A_S x + b))) and an FP64 reduction used only
+// for the sensitivity-normalisation check.
+#include <cuda_runtime.h>
+
+#include "jp_internal.cuh"
+
+namespace jp {
+namespace {
+
+__device__ __forceinline__ int frame_of(const int64_t* __restrict__ off, int n_frames, int64_t i) {
+  int lo = 0, hi = n_frames - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (__ldg(off + mid) <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void ratio_kernel(const float* __restrict__ p, const float* __restrict__ b,
+                             const int64_t* __restrict__ off, int n_frames, float* __restrict__ q,
+                             int64_t n) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (; i < n; i += stride) {
+    int f = (n_frames > 1) ? frame_of(off, n_frames, i) : 0;
+    q[i] = 1.0f / (p[i] + __ldg(b + f));
+  }
+}
+
+__global__ void update_kernel(float* __restrict__ x, const float* __restrict__ bp,
+                              const float* __restrict__ s, float scale, int64_t nvox, int n_frames,
+                              int64_t stride, int64_t s_stride) {
+  int64_t total = nvox * n_frames;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (; i < total; i += step) {
+    int64_t f = i / nvox, v = i - f * nvox;
+    float sv = s[f * s_stride + v] * scale;
+    float* xp = x + f * stride + v;
+    *xp = sv > 0.f ? *xp * bp[f * stride + v] / sv : 0.f;
+  }
+}
+
+__global__ void sum_f64_kernel(const float* __restrict__ x, int64_t n, double* out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t step = (int64_t)gridDim.x * blockDim.x;
+  for (; i < n; i += step) s += (double)x[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) atomicAdd(out, s);
+  }
+}
+
+int grid_for(int64_t n, int block) {
+  int64_t g = (n + block - 1) / block;
+  int64_t cap = (int64_t)sm_count() * 8;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+}  // namespace jp
+
+using namespace jp;
+
+extern "C" int jp_osem_ratio(jp_plan pl, const float* p, const float* b, float* q, int64_t n,
+                             void* stream) {
+  clear_error();
+  if (n < 0) return fail(JP_ERR_ARG, "n must be >= 0");
+  if (n > 0 && (!p || !b || !q)) return fail(JP_ERR_ARG, "NULL pointer");
+  if (!aligned(p, 4) || !aligned(b, 4) || !aligned(q, 4)) return fail(JP_ERR_ALIGN, "misaligned array");
+  const int64_t* off = nullptr;
+  int nf = 1;
+  if (pl) {
+    if (pl->n != n) return fail(JP_ERR_ARG, "n does not match the plan");
+    off = pl->frame_off_dev;
+    nf = pl->n_frames;
+  }
+  if (n == 0) return JP_OK;
+  ratio_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(p, b, off, nf, q, n);
+  count_launch();
+  JP_TRY_CUDA(cudaGetLastError());
+  return JP_OK;
+}
+
+extern "C" int jp_osem_update(float* x, const float* bp, const float* s, float scale, int64_t nvox,
+                              int32_t n_frames, int64_t stride, int64_t s_stride, void* stream) {
+  clear_error();
+  if (nvox < 0 || n_frames < 1 || stride < 0 || s_stride < 0) return fail(JP_ERR_ARG, "bad sizes");
+  if (n_frames > 1 && stride < nvox) return fail(JP_ERR_ARG, "img_stride smaller than nvox");
+  if (!(scale > 0.f) || !isfinite(scale)) return fail(JP_ERR_ARG, "scale must be finite and > 0");
+  if (nvox > 0 && (!x || !bp || !s)) return fail(JP_ERR_ARG, "NULL pointer");
+  if (!aligned(x, 4) || !aligned(bp, 4) || !aligned(s, 4)) return fail(JP_ERR_ALIGN, "misaligned array");
+  int64_t total = nvox * n_frames;
+  if (total == 0) return JP_OK;
+  update_kernel<<<grid_for(total, 256), 256, 0, (cudaStream_t)stream>>>(x, bp, s, scale, nvox, n_frames,
+                                                                       stride, s_stride);
+  count_launch();
+  JP_TRY_CUDA(cudaGetLastError());
+  return JP_OK;
+}
+
+extern "C" int jp_sum_f64(const float* x, int64_t n, double* out, void* stream) {
+  clear_error();
+  if (n < 0 || !out || (n > 0 && !x)) return fail(JP_ERR_ARG, "bad arguments");
+  if (!aligned(x, 4) || !aligned(out, 8)) return fail(JP_ERR_ALIGN, "misaligned array");
+  JP_TRY_CUDA(cudaMemsetAsync(out, 0, sizeof(double), (cudaStream_t)stream));
+  if (n == 0) return JP_OK;
+  sum_f64_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(x, n, out);
+  count_launch();
+  count_launch();
+  JP_TRY_CUDA(cudaGetLastError());
+  return JP_OK;
+}

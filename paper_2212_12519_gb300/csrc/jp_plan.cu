@@ -1,0 +1,383 @@
+// LOR plan: sorting LORs into coherent bins and packing them.
+//
+// Step a1 of the hot path.  The paper's kernels walk rays in input order and
+// report up to 7.6x run-time spread across memory orders (Sec. 3), traced to
+// races and cache behaviour (Sec. 4), and suggest pre-sorting events (Sec. 4).
+// Here each LOR gets a key
+//     frame | principal axis a | slope d_b/d_a | in-plane offset u at the
+//     centre plane | (listmode) TOF window centre along a
+// and a counting sort (histogram, exclusive scan, scatter) reorders the LORs
+// so that the 32 lanes of a warp follow nearly parallel, nearby rays whose
+// samples differ mainly along axis c -- the fastest-varying image axis for
+// a in {0,1}.  The sorted LORs are packed as two float4 (xs, delta) and
+// (xe, tof_bin) for 16-byte coalesced loads; perm maps back to caller order.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "jp_internal.cuh"
+
+namespace jp {
+
+namespace {
+
+constexpr int kScanBlock = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanBlock * kScanItems;
+
+__device__ __forceinline__ int frame_of(const int64_t* __restrict__ off, int n_frames, int64_t i) {
+  int lo = 0, hi = n_frames - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (__ldg(off + mid) <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+struct KeyParams {
+  const float* xs;
+  const float* xe;
+  const int16_t* tof_bin;
+  const float* delta;
+  int64_t n;
+  const int64_t* frame_off;
+  int n_frames;
+  DevGeom g;
+  int slope_bins, offset_bins, window_bins, keys_per_frame;
+  float tof_width;  // > 0: listmode window binning
+  int keep_order;
+};
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+__global__ void key_kernel(KeyParams p, uint32_t* __restrict__ keys, uint32_t* __restrict__ hist) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= p.n) return;
+  int f = frame_of(p.frame_off, p.n_frames, j);
+  uint32_t key = 0;
+  if (!p.keep_order) {
+    float xs[3] = {p.xs[3 * j], p.xs[3 * j + 1], p.xs[3 * j + 2]};
+    float xe[3] = {p.xe[3 * j], p.xe[3 * j + 1], p.xe[3 * j + 2]};
+    const float d0 = xe[0] - xs[0], d1 = xe[1] - xs[1], d2 = xe[2] - xs[2];
+    const int a = principal_axis(xs, xe);
+    const int b = (a == 0) ? 1 : 0;
+    const DevGeom& g = p.g;
+    const float da = sel3(a, d0, d1, d2), db = sel3(b, d0, d1, d2);
+    const float sb = (da != 0.f) ? db / da : 0.f;  // in [-1, 1]
+    const int qs = clampi((int)floorf((sb + 1.f) * 0.5f * (float)p.slope_bins), 0, p.slope_bins - 1);
+    // in-plane offset (continuous index along b) where the line crosses the centre plane
+    const int na = sel3(a, g.n[0], g.n[1], g.n[2]), nb = sel3(b, g.n[0], g.n[1], g.n[2]);
+    const float oa = sel3(a, g.o[0], g.o[1], g.o[2]), ob = sel3(b, g.o[0], g.o[1], g.o[2]);
+    const float va = sel3(a, g.v[0], g.v[1], g.v[2]), ivb = sel3(b, g.inv_v[0], g.inv_v[1], g.inv_v[2]);
+    const float kc = 0.5f * (float)(na - 1);
+    const float Xc = oa + kc * va;
+    const float ma = 0.5f * (sel3(a, xs[0], xs[1], xs[2]) + sel3(a, xe[0], xe[1], xe[2]));
+    const float mb = 0.5f * (sel3(b, xs[0], xs[1], xs[2]) + sel3(b, xe[0], xe[1], xe[2]));
+    const float t = (da != 0.f) ? (Xc - ma) / da : 0.f;
+    const float u = (fmaf(t, db, mb) - ob) * ivb;
+    const float cell_u = (float)(nb + 2) / (float)p.offset_bins;
+    const int qu = clampi((int)floorf((u + 1.f) / cell_u), 0, p.offset_bins - 1);
+    int qw = 0;
+    if (p.window_bins > 1 && p.tof_width > 0.f && p.tof_bin != nullptr) {
+      const float L = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+      const float cen = (float)p.tof_bin[j] * p.tof_width + (p.delta ? p.delta[j] : 0.f);
+      const float ca = (L > 0.f) ? ma + cen * da / L : ma;  // window centre along a
+      const float ka = (ca - oa) / va;
+      const float cell_a = (float)(na + 2) / (float)p.window_bins;
+      qw = clampi((int)floorf((ka + 1.f) / cell_a), 0, p.window_bins - 1);
+    }
+    key = (uint32_t)(((a * p.slope_bins + qs) * p.offset_bins + qu) * p.window_bins + qw);
+  }
+  key += (uint32_t)f * (uint32_t)p.keys_per_frame;
+  keys[j] = key;
+  if (!p.keep_order) atomicAdd(hist + key, 1u);
+}
+
+// exclusive scan, three passes: tile sums, scan of tile sums, tile scan
+__global__ void scan_tile_sums(const uint32_t* __restrict__ in, int64_t n, uint32_t* __restrict__ sums) {
+  __shared__ uint32_t red[kScanBlock / 32];
+  int64_t base = (int64_t)blockIdx.x * kScanTile;
+  uint32_t s = 0;
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) {
+    int64_t i = base + (int64_t)q * kScanBlock + threadIdx.x;
+    if (i < n) s += in[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = red[threadIdx.x];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) sums[blockIdx.x] = s;
+  }
+}
+
+// block-wide exclusive scan of kScanTile values held kScanItems per thread
+// (thread t holds items t*kScanItems .. t*kScanItems + kScanItems - 1)
+__device__ void block_exclusive_scan(uint32_t (&v)[kScanItems], uint32_t carry_in, uint32_t* total) {
+  __shared__ uint32_t warp_tot[kScanBlock / 32];
+  uint32_t local = 0;
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) { uint32_t x = v[q]; v[q] = local; local += x; }
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t incl = local;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) warp_tot[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t w = (lane < kScanBlock / 32) ? warp_tot[lane] : 0;
+    uint32_t wi = w;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += y;
+    }
+    if (lane < kScanBlock / 32) warp_tot[lane] = wi - w;  // exclusive
+    if (lane == 31 && total) *total = wi;
+  }
+  __syncthreads();
+  uint32_t off = carry_in + warp_tot[wid] + (incl - local);
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) v[q] += off;
+  __syncthreads();
+}
+
+// single CTA: exclusive scan of the tile sums (nt <= kScanTile)
+__global__ void scan_sums_kernel(uint32_t* __restrict__ sums, int64_t nt) {
+  uint32_t v[kScanItems];
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) {
+    int64_t i = (int64_t)threadIdx.x * kScanItems + q;
+    v[q] = i < nt ? sums[i] : 0u;
+  }
+  block_exclusive_scan(v, 0u, nullptr);
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) {
+    int64_t i = (int64_t)threadIdx.x * kScanItems + q;
+    if (i < nt) sums[i] = v[q];
+  }
+}
+
+__global__ void scan_apply_kernel(uint32_t* __restrict__ data, int64_t n, const uint32_t* __restrict__ sums) {
+  int64_t base = (int64_t)blockIdx.x * kScanTile;
+  uint32_t v[kScanItems];
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) {
+    int64_t i = base + (int64_t)threadIdx.x * kScanItems + q;
+    v[q] = i < n ? data[i] : 0u;
+  }
+  block_exclusive_scan(v, sums[blockIdx.x], nullptr);
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) {
+    int64_t i = base + (int64_t)threadIdx.x * kScanItems + q;
+    if (i < n) data[i] = v[q];
+  }
+}
+
+__global__ void scatter_kernel(KeyParams p, const uint32_t* __restrict__ keys, uint32_t* __restrict__ cursor,
+                               float4* __restrict__ lor, int32_t* __restrict__ perm) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= p.n) return;
+  uint32_t pos = p.keep_order ? (uint32_t)j : atomicAdd(cursor + keys[j], 1u);
+  float dl = p.delta ? p.delta[j] : 0.f;
+  int tb = p.tof_bin ? (int)p.tof_bin[j] : 0;
+  lor[2 * (int64_t)pos] = make_float4(p.xs[3 * j], p.xs[3 * j + 1], p.xs[3 * j + 2], dl);
+  lor[2 * (int64_t)pos + 1] = make_float4(p.xe[3 * j], p.xe[3 * j + 1], p.xe[3 * j + 2], __int_as_float(tb));
+  perm[pos] = (int32_t)j;
+}
+
+int validate_offsets(const int64_t* off, int32_t n_frames, int64_t* n_total) {
+  if (!off) return fail(JP_ERR_ARG, "frame_offsets is NULL");
+  if (n_frames < 1) return fail(JP_ERR_ARG, "n_frames must be >= 1");
+  if (off[0] != 0) return fail(JP_ERR_ARG, "frame_offsets[0] must be 0");
+  for (int32_t f = 0; f < n_frames; ++f)
+    if (off[f + 1] < off[f]) return fail(JP_ERR_ARG, "frame_offsets must be non-decreasing");
+  *n_total = off[n_frames];
+  if (*n_total >= (int64_t)INT32_MAX) return fail(JP_ERR_ARG, "n_total must be < 2^31");
+  return JP_OK;
+}
+
+int bind(jp_plan p, const float* xs, const float* xe, const int16_t* tof_bin, const float* delta,
+         const int64_t* off, int32_t n_frames, cudaStream_t st) {
+  int64_t n = 0;
+  int rc = validate_offsets(off, n_frames, &n);
+  if (rc) return rc;
+  if (n > p->capacity || n_frames > p->frame_capacity)
+    return fail(JP_ERR_ARG, "rebind exceeds the plan's capacity");
+  if (n > 0 && (!xs || !xe)) return fail(JP_ERR_ARG, "xstart/xend is NULL");
+  if (!aligned(xs, 4) || !aligned(xe, 4) || !aligned(tof_bin, 2) || !aligned(delta, 4))
+    return fail(JP_ERR_ALIGN, "misaligned LOR arrays");
+  p->has_tof_bin = tof_bin != nullptr;
+  p->has_delta = delta != nullptr;
+  DevGeom g;
+  rc = make_geom(&p->g, &g);
+  if (rc) return rc;
+  std::memcpy(p->frame_off_host, off, sizeof(int64_t) * (n_frames + 1));
+  JP_TRY_CUDA(cudaMemcpyAsync(p->frame_off_dev, p->frame_off_host, sizeof(int64_t) * (n_frames + 1),
+                              cudaMemcpyHostToDevice, st));
+  p->n = n;
+  p->n_frames = n_frames;
+  if (n == 0) return JP_OK;
+  KeyParams kp;
+  kp.xs = xs; kp.xe = xe; kp.tof_bin = tof_bin; kp.delta = delta; kp.n = n;
+  kp.frame_off = p->frame_off_dev; kp.n_frames = n_frames; kp.g = g;
+  kp.slope_bins = p->dims.slope_bins; kp.offset_bins = p->dims.offset_bins;
+  kp.window_bins = p->dims.window_bins; kp.keys_per_frame = p->dims.keys_per_frame;
+  kp.tof_width = p->opts.tof_bin_width;
+  kp.keep_order = (p->opts.flags & JP_PLAN_KEEP_ORDER) ? 1 : 0;
+  int64_t hist_len = (int64_t)n_frames * p->dims.keys_per_frame;
+  int blocks = (int)((n + 255) / 256);
+  if (!kp.keep_order) {
+    JP_TRY_CUDA(cudaMemsetAsync(p->hist, 0, sizeof(uint32_t) * hist_len, st));
+  }
+  key_kernel<<<blocks, 256, 0, st>>>(kp, p->keys, p->hist);
+  count_launch();
+  JP_TRY_CUDA(cudaGetLastError());
+  if (!kp.keep_order) {
+    int64_t nt = (hist_len + kScanTile - 1) / kScanTile;
+    scan_tile_sums<<<(unsigned)nt, kScanBlock, 0, st>>>(p->hist, hist_len, p->block_sums);
+    count_launch();
+    scan_sums_kernel<<<1, kScanBlock, 0, st>>>(p->block_sums, nt);
+    count_launch();
+    scan_apply_kernel<<<(unsigned)nt, kScanBlock, 0, st>>>(p->hist, hist_len, p->block_sums);
+    count_launch();
+    JP_TRY_CUDA(cudaGetLastError());
+  }
+  scatter_kernel<<<blocks, 256, 0, st>>>(kp, p->keys, p->hist, p->lor, p->perm);
+  count_launch();
+  JP_TRY_CUDA(cudaGetLastError());
+  return JP_OK;
+}
+
+void free_plan(jp_plan p) {
+  if (!p) return;
+  cudaFree(p->lor);
+  cudaFree(p->perm);
+  cudaFree(p->keys);
+  cudaFree(p->hist);
+  cudaFree(p->block_sums);
+  cudaFree(p->frame_off_dev);
+  cudaFreeHost(p->frame_off_host);
+  delete p;
+}
+
+}  // namespace
+
+}  // namespace jp
+
+using namespace jp;
+
+extern "C" int jp_plan_create_batch(jp_plan* out, const float* xs, const float* xe,
+                                    const int16_t* tof_bin, const float* delta,
+                                    const int64_t* off, int32_t n_frames, const jp_image_geom* g,
+                                    const jp_plan_opts* opts, void* stream) {
+  clear_error();
+  if (!out) return fail(JP_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!g) return fail(JP_ERR_ARG, "geometry is NULL");
+  DevGeom dg;
+  int rc = make_geom(g, &dg);
+  if (rc) return rc;
+  int64_t n = 0;
+  rc = validate_offsets(off, n_frames, &n);
+  if (rc) return rc;
+  jp_plan_opts o;
+  std::memset(&o, 0, sizeof(o));
+  if (opts) o = *opts;
+  if (o.block == 0) o.block = 256;
+  if (o.block < 64 || o.block > 1024 || (o.block % 32) != 0) return fail(JP_ERR_ARG, "opts.block must be 64..1024, multiple of 32");
+  if (o.slope_bins == 0) o.slope_bins = 64;
+  if (o.offset_bins == 0) o.offset_bins = 64;
+  if (o.window_bins == 0) o.window_bins = 16;
+  if (o.slope_bins < 1 || o.offset_bins < 1 || o.window_bins < 1) return fail(JP_ERR_ARG, "bin counts must be >= 1");
+  if (!(o.tof_bin_width >= 0.f) || !isfinite(o.tof_bin_width)) return fail(JP_ERR_ARG, "opts.tof_bin_width must be finite and >= 0");
+  int window_bins = (o.tof_bin_width > 0.f && tof_bin) ? o.window_bins : 1;
+  int64_t kpf = 3LL * o.slope_bins * o.offset_bins * window_bins;
+  if (o.flags & JP_PLAN_KEEP_ORDER) kpf = 1;
+  if (kpf * (int64_t)n_frames >= (int64_t)kScanTile * kScanTile)
+    return fail(JP_ERR_ARG, "too many bins (n_frames * 3 * slope * offset * window >= 2^24)");
+  jp_plan p = new (std::nothrow) jp_plan_s();
+  if (!p) return fail(JP_ERR_NOMEM, "host allocation failed");
+  std::memset(p, 0, sizeof(*p));
+  p->capacity = n;
+  p->frame_capacity = n_frames;
+  p->g = *g;
+  p->opts = o;
+  p->dims.slope_bins = o.slope_bins;
+  p->dims.offset_bins = o.offset_bins;
+  p->dims.window_bins = window_bins;
+  p->dims.keys_per_frame = (int)kpf;
+  p->has_tof_bin = tof_bin != nullptr;
+  p->has_delta = delta != nullptr;
+  p->hist_len = kpf * n_frames;
+  p->scan_blocks_cap = (p->hist_len + kScanTile - 1) / kScanTile;
+  p->n = 0;
+  size_t nn = (size_t)std::max<int64_t>(n, 1);
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaMalloc(&p->lor, sizeof(float4) * 2 * nn);
+  if (e == cudaSuccess) e = cudaMalloc(&p->perm, sizeof(int32_t) * nn);
+  if (e == cudaSuccess) e = cudaMalloc(&p->keys, sizeof(uint32_t) * nn);
+  if (e == cudaSuccess) e = cudaMalloc(&p->hist, sizeof(uint32_t) * (p->hist_len + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&p->block_sums, sizeof(uint32_t) * (p->scan_blocks_cap + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&p->frame_off_dev, sizeof(int64_t) * (n_frames + 1));
+  if (e == cudaSuccess) e = cudaMallocHost(&p->frame_off_host, sizeof(int64_t) * (n_frames + 1));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    free_plan(p);
+    return fail(e == cudaErrorMemoryAllocation ? JP_ERR_NOMEM : JP_ERR_CUDA,
+                std::string("plan allocation: ") + cudaGetErrorString(e));
+  }
+  rc = bind(p, xs, xe, tof_bin, delta, off, n_frames, (cudaStream_t)stream);
+  if (rc) {
+    free_plan(p);
+    return rc;
+  }
+  *out = p;
+  return JP_OK;
+}
+
+extern "C" int jp_plan_create(jp_plan* out, const float* xs, const float* xe,
+                              const int16_t* tof_bin, const float* delta, int64_t n_lor,
+                              const jp_image_geom* g, const jp_plan_opts* opts, void* stream) {
+  if (n_lor < 0) {
+    clear_error();
+    return fail(JP_ERR_ARG, "n_lor must be >= 0");
+  }
+  int64_t off[2] = {0, n_lor};
+  return jp_plan_create_batch(out, xs, xe, tof_bin, delta, off, 1, g, opts, stream);
+}
+
+extern "C" int jp_plan_rebind(jp_plan p, const float* xs, const float* xe, const int16_t* tof_bin,
+                              const float* delta, const int64_t* off, int32_t n_frames,
+                              void* stream) {
+  clear_error();
+  if (!p) return fail(JP_ERR_ARG, "plan is NULL");
+  return bind(p, xs, xe, tof_bin, delta, off, n_frames, (cudaStream_t)stream);
+}
+
+extern "C" int jp_plan_destroy(jp_plan p) {
+  clear_error();
+  if (!p) return JP_OK;
+  cudaDeviceSynchronize();
+  free_plan(p);
+  return JP_OK;
+}
+
+extern "C" int jp_plan_info(jp_plan p, int64_t* n_lor, int32_t* n_frames, int32_t* perm_out,
+                            void* stream) {
+  clear_error();
+  if (!p) return fail(JP_ERR_ARG, "plan is NULL");
+  if (n_lor) *n_lor = p->n;
+  if (n_frames) *n_frames = p->n_frames;
+  if (perm_out && p->n > 0) {
+    if (!aligned(perm_out, 4)) return fail(JP_ERR_ALIGN, "perm_out must be 4-byte aligned");
+    JP_TRY_CUDA(cudaMemcpyAsync(perm_out, p->perm, sizeof(int32_t) * p->n, cudaMemcpyDeviceToDevice,
+                                (cudaStream_t)stream));
+  }
+  return JP_OK;
+}

@@ -1,0 +1,371 @@
+"""Thin ctypes binding of libjoseph (declared in include/joseph.h).
+
+Argument marshalling only: every function converts torch CUDA tensors into
+device pointers, passes the current CUDA stream and raises ``JosephError``
+on a non-zero status.  All compute runs in the library's CUDA kernels; there
+is no CPU path.  Function names mirror the C entry points (``jp_fwd`` ...);
+short aliases (``fwd`` ...) are provided for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional, Sequence
+
+import torch
+
+from . import build as _build
+
+P = ctypes.c_void_p
+I32 = ctypes.c_int32
+I64 = ctypes.c_int64
+F32 = ctypes.c_float
+
+TOF_MODES = {"nontof": 0, "tof_sino": 1, "tof_lm": 2}
+JP_PLAN_KEEP_ORDER = 1
+
+
+class JosephError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libjoseph error {code}: {msg}")
+        self.code = code
+
+
+class ImageGeomC(ctypes.Structure):
+    _fields_ = [("n", I32 * 3), ("origin", F32 * 3), ("voxsize", F32 * 3)]
+
+
+class TofC(ctypes.Structure):
+    _fields_ = [("bin_width", F32), ("sigma", F32), ("n_sigmas", F32), ("n_bins", I32)]
+
+
+class PlanOptsC(ctypes.Structure):
+    _fields_ = [("block", I32), ("slope_bins", I32), ("offset_bins", I32), ("window_bins", I32),
+                ("tof_bin_width", F32), ("flags", I32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+_SIGS = {
+    "jp_plan_create_batch": [ctypes.POINTER(P), P, P, P, P, P, I32, P, P, P],
+    "jp_plan_create": [ctypes.POINTER(P), P, P, P, P, I64, P, P, P],
+    "jp_plan_rebind": [P, P, P, P, P, P, I32, P],
+    "jp_plan_destroy": [P],
+    "jp_plan_info": [P, P, P, P, P],
+    "jp_fwd": [P, P, I64, P, P],
+    "jp_back": [P, P, P, I64, P],
+    "jp_fwd_tof_sino": [P, P, I64, P, P, P],
+    "jp_back_tof_sino": [P, P, P, P, I64, P],
+    "jp_fwd_tof_lm": [P, P, I64, P, P, P],
+    "jp_back_tof_lm": [P, P, P, P, I64, P],
+    "jp_fwd_lors": [P, P, P, P, I64, P, I32, P, P, P, P],
+    "jp_back_lors": [P, P, P, P, I64, P, I32, P, P, P, P],
+    "jp_osem_ratio": [P, P, P, P, I64, P],
+    "jp_osem_update": [P, P, P, F32, I64, I32, I64, I64, P],
+    "jp_sum_f64": [P, I64, P, P],
+    "jp_count_samples": [P, I32, P, P, P],
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Loads the in-tree libjoseph.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libjoseph is not built ({path}); run paper_2212_12519_gb300.build.build()")
+        lib = ctypes.CDLL(path)
+        for name, args in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        lib.jp_launch_count.restype = ctypes.c_uint64
+        lib.jp_launch_count.argtypes = []
+        lib.jp_last_error.restype = ctypes.c_char_p
+        lib.jp_version.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise JosephError(rc, load().jp_last_error().decode())
+
+
+def _stream(stream=None) -> P:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return P(s.cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor], dtype=None, name="tensor"):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return P(t.data_ptr())
+
+
+def image_geom(geom) -> ImageGeomC:
+    g = ImageGeomC()
+    for i in range(3):
+        g.n[i] = int(geom.shape[i])
+        g.origin[i] = float(geom.origin[i])
+        g.voxsize[i] = float(geom.voxsize[i])
+    return g
+
+
+def tof_params(tof) -> TofC:
+    return TofC(float(tof.bin_width), float(tof.sigma), float(tof.n_sigmas), int(tof.n_bins))
+
+
+def _lors(xs, xe):
+    if xs.dim() != 2 or xs.shape[1] != 3 or xs.shape != xe.shape:
+        raise ValueError("xstart/xend must be [n, 3]")
+    return _ptr(xs, torch.float32, "xstart"), _ptr(xe, torch.float32, "xend")
+
+
+# ---------------------------------------------------------------------------
+# plans
+# ---------------------------------------------------------------------------
+class Plan:
+    """Owns a libjoseph plan (sorted, packed LORs of one or more frames)."""
+
+    def __init__(self, handle: int, geom, n: int, n_frames: int, frame_offsets: Sequence[int],
+                 has_tof_bin: bool):
+        self._h = P(handle)
+        self.geom = geom
+        self.n = n
+        self.n_frames = n_frames
+        self.frame_offsets = list(frame_offsets)
+        self.has_tof_bin = has_tof_bin
+
+    @property
+    def handle(self):
+        if self._h is None or not self._h.value:
+            raise RuntimeError("plan has been destroyed")
+        return self._h
+
+    def perm(self, stream=None) -> torch.Tensor:
+        """A copy of the plan's permutation (binned position -> caller index)."""
+        out = torch.empty(self.n, dtype=torch.int32, device="cuda")
+        _check(load().jp_plan_info(self.handle, None, None, _ptr(out, torch.int32, "perm"), _stream(stream)))
+        return out
+
+    def destroy(self):
+        if self._h is not None and self._h.value:
+            _check(load().jp_plan_destroy(self._h))
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def _opts(block=0, slope_bins=0, offset_bins=0, window_bins=0, tof_bin_width=0.0, keep_order=False):
+    return PlanOptsC(int(block), int(slope_bins), int(offset_bins), int(window_bins),
+                     float(tof_bin_width), JP_PLAN_KEEP_ORDER if keep_order else 0)
+
+
+def jp_plan_create_batch(xs, xe, geom, frame_offsets, tof_bin=None, delta=None, stream=None,
+                         **opts) -> Plan:
+    pxs, pxe = _lors(xs, xe)
+    off = (ctypes.c_int64 * len(frame_offsets))(*[int(v) for v in frame_offsets])
+    h = P()
+    g = image_geom(geom)
+    o = _opts(**opts)
+    _check(load().jp_plan_create_batch(ctypes.byref(h), pxs, pxe, _ptr(tof_bin, torch.int16, "tof_bin"),
+                                       _ptr(delta, torch.float32, "delta"), off, len(frame_offsets) - 1,
+                                       ctypes.byref(g), ctypes.byref(o), _stream(stream)))
+    return Plan(h.value, geom, int(frame_offsets[-1]), len(frame_offsets) - 1, frame_offsets,
+                tof_bin is not None)
+
+
+def jp_plan_create(xs, xe, geom, tof_bin=None, delta=None, stream=None, **opts) -> Plan:
+    return jp_plan_create_batch(xs, xe, geom, [0, int(xs.shape[0])], tof_bin, delta, stream, **opts)
+
+
+def jp_plan_rebind(plan: Plan, xs, xe, frame_offsets=None, tof_bin=None, delta=None, stream=None):
+    pxs, pxe = _lors(xs, xe)
+    if frame_offsets is None:
+        frame_offsets = [0, int(xs.shape[0])]
+    off = (ctypes.c_int64 * len(frame_offsets))(*[int(v) for v in frame_offsets])
+    _check(load().jp_plan_rebind(plan.handle, pxs, pxe, _ptr(tof_bin, torch.int16, "tof_bin"),
+                                 _ptr(delta, torch.float32, "delta"), off, len(frame_offsets) - 1,
+                                 _stream(stream)))
+    plan.n = int(frame_offsets[-1])
+    plan.n_frames = len(frame_offsets) - 1
+    plan.frame_offsets = list(frame_offsets)
+    plan.has_tof_bin = tof_bin is not None
+
+
+def jp_plan_destroy(plan: Plan):
+    plan.destroy()
+
+
+# ---------------------------------------------------------------------------
+# projections
+# ---------------------------------------------------------------------------
+def _img_stride(plan: Plan, img: torch.Tensor, img_stride):
+    if img_stride is not None:
+        return int(img_stride)
+    nvox = int(plan.geom.shape[0] * plan.geom.shape[1] * plan.geom.shape[2])
+    if img.numel() == nvox:
+        return 0
+    if img.numel() == nvox * plan.n_frames:
+        return nvox
+    raise ValueError("image size matches neither one image nor one per frame")
+
+
+def jp_fwd(plan: Plan, img, out=None, img_stride=None, stream=None):
+    out = torch.empty(plan.n, dtype=torch.float32, device=img.device) if out is None else out
+    _check(load().jp_fwd(plan.handle, _ptr(img, torch.float32, "img"), _img_stride(plan, img, img_stride),
+                         _ptr(out, torch.float32, "proj"), _stream(stream)))
+    return out
+
+
+def jp_back(plan: Plan, proj, img_accum, img_stride=None, stream=None):
+    _check(load().jp_back(plan.handle, _ptr(proj, torch.float32, "proj"),
+                          _ptr(img_accum, torch.float32, "img_accum"),
+                          _img_stride(plan, img_accum, img_stride), _stream(stream)))
+    return img_accum
+
+
+def jp_fwd_tof_sino(plan: Plan, img, tof, out=None, img_stride=None, stream=None):
+    if out is None:
+        out = torch.empty((plan.n, int(tof.n_bins)), dtype=torch.float32, device=img.device)
+    t = tof_params(tof)
+    _check(load().jp_fwd_tof_sino(plan.handle, _ptr(img, torch.float32, "img"),
+                                  _img_stride(plan, img, img_stride), ctypes.byref(t),
+                                  _ptr(out, torch.float32, "proj"), _stream(stream)))
+    return out
+
+
+def jp_back_tof_sino(plan: Plan, proj, tof, img_accum, img_stride=None, stream=None):
+    t = tof_params(tof)
+    _check(load().jp_back_tof_sino(plan.handle, _ptr(proj, torch.float32, "proj"), ctypes.byref(t),
+                                   _ptr(img_accum, torch.float32, "img_accum"),
+                                   _img_stride(plan, img_accum, img_stride), _stream(stream)))
+    return img_accum
+
+
+def jp_fwd_tof_lm(plan: Plan, img, tof, out=None, img_stride=None, stream=None):
+    out = torch.empty(plan.n, dtype=torch.float32, device=img.device) if out is None else out
+    t = tof_params(tof)
+    _check(load().jp_fwd_tof_lm(plan.handle, _ptr(img, torch.float32, "img"),
+                                _img_stride(plan, img, img_stride), ctypes.byref(t),
+                                _ptr(out, torch.float32, "proj"), _stream(stream)))
+    return out
+
+
+def jp_back_tof_lm(plan: Plan, proj, tof, img_accum, img_stride=None, stream=None):
+    t = tof_params(tof)
+    _check(load().jp_back_tof_lm(plan.handle, _ptr(proj, torch.float32, "proj"), ctypes.byref(t),
+                                 _ptr(img_accum, torch.float32, "img_accum"),
+                                 _img_stride(plan, img_accum, img_stride), _stream(stream)))
+    return img_accum
+
+
+def jp_fwd_lors(xs, xe, img, geom, tof_mode="nontof", tof=None, tof_bin=None, delta=None, out=None,
+                stream=None):
+    m = TOF_MODES[tof_mode]
+    n = int(xs.shape[0])
+    if out is None:
+        shape = (n, int(tof.n_bins)) if m == 1 else (n,)
+        out = torch.empty(shape, dtype=torch.float32, device=img.device)
+    pxs, pxe = _lors(xs, xe)
+    g = image_geom(geom)
+    t = tof_params(tof) if tof is not None else None
+    _check(load().jp_fwd_lors(pxs, pxe, _ptr(tof_bin, torch.int16, "tof_bin"), _ptr(delta, torch.float32, "delta"),
+                              n, ctypes.byref(g), m, ctypes.byref(t) if t is not None else None,
+                              _ptr(img, torch.float32, "img"), _ptr(out, torch.float32, "proj"), _stream(stream)))
+    return out
+
+
+def jp_back_lors(xs, xe, proj, geom, img_accum, tof_mode="nontof", tof=None, tof_bin=None, delta=None,
+                 stream=None):
+    m = TOF_MODES[tof_mode]
+    pxs, pxe = _lors(xs, xe)
+    g = image_geom(geom)
+    t = tof_params(tof) if tof is not None else None
+    _check(load().jp_back_lors(pxs, pxe, _ptr(tof_bin, torch.int16, "tof_bin"), _ptr(delta, torch.float32, "delta"),
+                               int(xs.shape[0]), ctypes.byref(g), m, ctypes.byref(t) if t is not None else None,
+                               _ptr(proj, torch.float32, "proj"), _ptr(img_accum, torch.float32, "img_accum"),
+                               _stream(stream)))
+    return img_accum
+
+
+# ---------------------------------------------------------------------------
+# OSEM element-wise steps and FP64 check sum
+# ---------------------------------------------------------------------------
+def jp_osem_ratio(plan: Optional[Plan], proj, b, out=None, stream=None):
+    out = proj if out is None else out
+    _check(load().jp_osem_ratio(plan.handle if plan is not None else None, _ptr(proj, torch.float32, "proj"),
+                                _ptr(b, torch.float32, "b"), _ptr(out, torch.float32, "q"), int(proj.numel()),
+                                _stream(stream)))
+    return out
+
+
+def jp_osem_update(x, bp, sens, scale, nvox, n_frames=1, img_stride=None, s_stride=0, stream=None):
+    img_stride = nvox if img_stride is None else img_stride
+    _check(load().jp_osem_update(_ptr(x, torch.float32, "x"), _ptr(bp, torch.float32, "bp"),
+                                 _ptr(sens, torch.float32, "sens"), float(scale), int(nvox), int(n_frames),
+                                 int(img_stride), int(s_stride), _stream(stream)))
+    return x
+
+
+def jp_sum_f64(x, out=None, stream=None):
+    out = torch.empty((), dtype=torch.float64, device=x.device) if out is None else out
+    _check(load().jp_sum_f64(_ptr(x, torch.float32, "x"), int(x.numel()), _ptr(out, torch.float64, "out"),
+                             _stream(stream)))
+    return out
+
+
+def jp_count_samples(plan: Plan, tof_mode="nontof", tof=None, stream=None) -> int:
+    """Plane samples visited by the projector for the plan's LORs (exact)."""
+    out = torch.zeros((), dtype=torch.int64, device="cuda")
+    t = tof_params(tof) if tof is not None else None
+    _check(load().jp_count_samples(plan.handle, TOF_MODES[tof_mode], ctypes.byref(t) if t is not None else None,
+                                   _ptr(out, None, "out"), _stream(stream)))
+    return int(out.item())
+
+
+def jp_launch_count() -> int:
+    """Kernels launched by libjoseph so far in this process."""
+    return int(load().jp_launch_count())
+
+
+def jp_version() -> str:
+    return load().jp_version().decode()
+
+
+# short aliases
+plan_create = jp_plan_create
+plan_create_batch = jp_plan_create_batch
+plan_rebind = jp_plan_rebind
+fwd = jp_fwd
+back = jp_back
+fwd_tof_sino = jp_fwd_tof_sino
+back_tof_sino = jp_back_tof_sino
+fwd_tof_lm = jp_fwd_tof_lm
+back_tof_lm = jp_back_tof_lm
+fwd_lors = jp_fwd_lors
+back_lors = jp_back_lors
+osem_ratio = jp_osem_ratio
+osem_update = jp_osem_update
+sum_f64 = jp_sum_f64

@@ -1,0 +1,276 @@
+"""GPU (CUDA, sm_103a) vs FP64 oracle parity, element by element, at sizes
+the oracle finishes in seconds (several CTAs and a ragged tail), plus edge
+cases.  Forward: max|err| <= 1e-5 max|oracle| (TOF-window decisions inside
+the FP32/FP64 rounding band excepted); back: relative L2 <= 1e-4."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2212_12519_gb300 import synth
+from _parity import AMB_EPS, BACK_TOL, FWD_TOL, fwd_err, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+THREADS = 8
+
+
+@pytest.fixture(scope="module")
+def ops():
+    from paper_2212_12519_gb300 import build, ops as _ops
+    build.build()
+    _ops.load()
+    return _ops
+
+
+def cuda(a, dtype=None):
+    t = torch.as_tensor(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda().contiguous()
+
+
+# ---------------------------------------------------------------------------
+# small sinogram workload (266,240 LORs, 64x64x16), non-TOF
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def small():
+    g = synth.GEOM_SMALL
+    img = synth.ellipsoid_phantom(g, synth.PHANTOM_SMALL, 1001).numpy()
+    xs, xe = synth.sinogram_lors(synth.SINO_SMALL)
+    xs, xe = xs.numpy(), xe.numpy()
+    y = synth.uniform_values(len(xs), 1002)
+    p_or = oracle.fwd(xs, xe, img, g, threads=THREADS)
+    b_or = oracle.back(xs, xe, y, g, threads=THREADS)
+    return g, img, xs, xe, y, p_or, b_or
+
+
+@pytest.mark.parametrize("planned", [True, False])
+def test_small_nontof(ops, small, planned):
+    g, img, xs, xe, y, p_or, b_or = small
+    dxs, dxe, dimg, dy = cuda(xs), cuda(xe), cuda(img), cuda(y)
+    out = torch.zeros(g.shape, device="cuda")
+    if planned:
+        plan = ops.jp_plan_create(dxs, dxe, g)
+        p = ops.jp_fwd(plan, dimg)
+        ops.jp_back(plan, dy, out)
+    else:
+        p = ops.jp_fwd_lors(dxs, dxe, dimg, g)
+        ops.jp_back_lors(dxs, dxe, dy, g, out)
+    torch.cuda.synchronize()
+    assert fwd_err(p.cpu().numpy(), p_or) <= FWD_TOL
+    assert rel_l2(out.cpu().numpy(), b_or) <= BACK_TOL
+
+
+def test_plan_permutation_is_a_permutation(ops, small):
+    g, img, xs, xe, *_ = small
+    plan = ops.jp_plan_create(cuda(xs), cuda(xe), g)
+    perm = plan.perm().cpu().numpy()
+    assert np.array_equal(np.sort(perm), np.arange(len(xs)))
+    keep = ops.jp_plan_create(cuda(xs), cuda(xe), g, keep_order=True)
+    assert np.array_equal(keep.perm().cpu().numpy(), np.arange(len(xs)))
+
+
+def test_forward_is_deterministic(ops, small):
+    g, img, xs, xe, *_ = small
+    plan = ops.jp_plan_create(cuda(xs), cuda(xe), g)
+    a = ops.jp_fwd(plan, cuda(img)).cpu()
+    plan2 = ops.jp_plan_create(cuda(xs), cuda(xe), g, slope_bins=7, offset_bins=5)
+    b = ops.jp_fwd(plan2, cuda(img)).cpu()
+    c = ops.jp_fwd_lors(cuda(xs), cuda(xe), cuda(img), g).cpu()
+    assert torch.equal(a, b) and torch.equal(a, c)
+
+
+# ---------------------------------------------------------------------------
+# clinical image, TOF sinogram (a subset of views/planes of the TOF sinogram)
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def clinical_img():
+    return synth.ellipsoid_phantom(synth.GEOM_CLINICAL, synth.PHANTOM_CLINICAL, 2001).numpy()
+
+
+def tof_sino_subset(n_planes=24, view_step=16):
+    spec = synth.SinoSpec(synth.SCANNER_CLINICAL, 336, 313, view_step=view_step)
+    xs, xe = synth.sinogram_lors(spec, plane_range=(0, 1296))
+    # a spread of planes (ring pairs), every view_step-th view
+    idx = np.linspace(0, 1295, n_planes).astype(np.int64)
+    per = len(spec.views) * spec.n_rad
+    sel = (idx[:, None] * per + np.arange(per)[None, :]).ravel()
+    return xs.numpy()[sel], xe.numpy()[sel]
+
+
+@pytest.mark.parametrize("planned", [True, False])
+def test_tof_sino(ops, clinical_img, planned):
+    g = synth.GEOM_CLINICAL
+    tof = synth.TOF_CLINICAL
+    xs, xe = tof_sino_subset()
+    n = len(xs)
+    y = synth.poisson_values((n, tof.n_bins), 3002)
+    p_or, amb = oracle.fwd(xs, xe, clinical_img, g, "tof_sino", tof, threads=THREADS,
+                           amb_eps=AMB_EPS, return_amb=True)
+    b_or = oracle.back(xs, xe, y, g, "tof_sino", tof, threads=THREADS)
+    out = torch.zeros(g.shape, device="cuda")
+    if planned:
+        plan = ops.jp_plan_create(cuda(xs), cuda(xe), g)
+        p = ops.jp_fwd_tof_sino(plan, cuda(clinical_img), tof)
+        ops.jp_back_tof_sino(plan, cuda(y), tof, out)
+    else:
+        p = ops.jp_fwd_lors(cuda(xs), cuda(xe), cuda(clinical_img), g, "tof_sino", tof)
+        ops.jp_back_lors(cuda(xs), cuda(xe), cuda(y), g, out, "tof_sino", tof)
+    torch.cuda.synchronize()
+    assert fwd_err(p.cpu().numpy(), p_or, amb) <= FWD_TOL
+    assert rel_l2(out.cpu().numpy(), b_or) <= BACK_TOL
+
+
+# ---------------------------------------------------------------------------
+# TOF listmode
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def lm_events(clinical_img):
+    g = synth.GEOM_CLINICAL
+    xs, xe, tb = synth.lm_events(torch.from_numpy(clinical_img), g, synth.SCANNER_CLINICAL,
+                                 synth.TOF_CLINICAL, 300_001, seed=4101)
+    return xs.numpy(), xe.numpy(), tb.numpy()
+
+
+@pytest.mark.parametrize("planned", [True, False])
+def test_tof_lm(ops, clinical_img, lm_events, planned):
+    g = synth.GEOM_CLINICAL
+    tof = synth.TOF_CLINICAL
+    xs, xe, tb = lm_events
+    y = synth.uniform_values(len(xs), 4102, 0.5, 1.5)
+    p_or, amb = oracle.fwd(xs, xe, clinical_img, g, "tof_lm", tof, tof_bin=tb, threads=THREADS,
+                           amb_eps=AMB_EPS, return_amb=True)
+    b_or = oracle.back(xs, xe, y, g, "tof_lm", tof, tof_bin=tb, threads=THREADS)
+    out = torch.zeros(g.shape, device="cuda")
+    dtb = cuda(tb, torch.int16)
+    if planned:
+        plan = ops.jp_plan_create(cuda(xs), cuda(xe), g, tof_bin=dtb, tof_bin_width=tof.bin_width)
+        p = ops.jp_fwd_tof_lm(plan, cuda(clinical_img), tof)
+        ops.jp_back_tof_lm(plan, cuda(y), tof, out)
+    else:
+        p = ops.jp_fwd_lors(cuda(xs), cuda(xe), cuda(clinical_img), g, "tof_lm", tof, tof_bin=dtb)
+        ops.jp_back_lors(cuda(xs), cuda(xe), cuda(y), g, out, "tof_lm", tof, tof_bin=dtb)
+    torch.cuda.synchronize()
+    assert fwd_err(p.cpu().numpy(), p_or, amb) <= FWD_TOL
+    assert rel_l2(out.cpu().numpy(), b_or) <= BACK_TOL
+
+
+def test_tof_offsets_and_nonisotropic(ops):
+    """Per-LOR TOF centre offsets, non-isotropic voxels, an off-centre origin
+    and LORs starting/ending inside the image, all three TOF modes."""
+    g = synth.ImageGeom((37, 29, 23), (-40.0, -25.0, -20.5), (2.1, 1.7, 1.9))
+    rng = np.random.Generator(np.random.PCG64(5001))
+    img = rng.uniform(0, 3, size=g.shape).astype(np.float32)
+    xs1, xe1 = synth.random_lors(40_000, g, seed=5002)
+    xs2, xe2 = synth.random_lors(9_000, g, seed=5003, kind="inside")
+    xs, xe = np.concatenate([xs1, xs2]), np.concatenate([xe1, xe2])
+    n = len(xs)
+    tof = synth.TofParams(bin_width=9.0, sigma=7.0, n_sigmas=3.0, n_bins=15)
+    delta = rng.normal(0, 4, size=n).astype(np.float32)
+    tb = rng.integers(-7, 8, size=n).astype(np.int16)
+    for mode in ["nontof", "tof_sino", "tof_lm"]:
+        t = None if mode == "nontof" else tof
+        kw = dict(tof_bin=tb) if mode == "tof_lm" else {}
+        p_or, amb = oracle.fwd(xs, xe, img, g, mode, t, delta=delta if mode != "nontof" else None,
+                               threads=THREADS, amb_eps=AMB_EPS, return_amb=True, **kw)
+        nout = tof.n_bins if mode == "tof_sino" else 1
+        y = rng.uniform(0, 1, size=n * nout).astype(np.float32)
+        b_or = oracle.back(xs, xe, y, g, mode, t, delta=delta if mode != "nontof" else None,
+                           threads=THREADS, **kw)
+        plan = ops.jp_plan_create(cuda(xs), cuda(xe), g, tof_bin=cuda(tb),
+                                  delta=cuda(delta), tof_bin_width=tof.bin_width)
+        out = torch.zeros(g.shape, device="cuda")
+        dy = cuda(y.reshape((n, nout)) if mode == "tof_sino" else y)
+        if mode == "nontof":
+            p = ops.jp_fwd(plan, cuda(img))
+            ops.jp_back(plan, dy, out)
+        elif mode == "tof_sino":
+            p = ops.jp_fwd_tof_sino(plan, cuda(img), tof)
+            ops.jp_back_tof_sino(plan, dy, tof, out)
+        else:
+            p = ops.jp_fwd_tof_lm(plan, cuda(img), tof)
+            ops.jp_back_tof_lm(plan, dy, tof, out)
+        torch.cuda.synchronize()
+        assert fwd_err(p.cpu().numpy(), p_or, amb) <= FWD_TOL, mode
+        assert rel_l2(out.cpu().numpy(), b_or) <= BACK_TOL, mode
+
+
+def test_edge_cases(ops):
+    """Empty input, degenerate LORs, misses, axis-aligned rays, exact
+    principal-axis ties, every principal axis including axis 2."""
+    g = synth.ImageGeom((9, 8, 7), (-4.0, -3.5, -3.0), (1.0, 1.0, 1.0))
+    rng = np.random.Generator(np.random.PCG64(6001))
+    img = rng.uniform(0, 2, size=g.shape).astype(np.float32)
+    xs = [(0.1, 0.2, 0.3), (-20, 30, 5), (-20, 0.0, 0.0), (0.5, -20, 0.5), (0.25, -0.5, -20),
+          (-6.0, -6.3, -0.9), (-4.0, 1.0, -4.1), (-3.0, -2.0, -9.0), (-9.0, 0.0, 0.0)]
+    xe = [(0.1, 0.2, 0.3), (20, 30, 5), (20, 0.0, 0.0), (0.5, 20, 0.5), (0.25, -0.5, 20),
+          (6.0, 5.7, 0.8), (4.0, -0.3, 3.9), (2.0, 2.5, 9.0), (0.0, 0.0, 0.0)]
+    xs = np.asarray(xs, np.float32)
+    xe = np.asarray(xe, np.float32)
+    p_or = oracle.fwd(xs, xe, img, g)
+    p = ops.jp_fwd_lors(cuda(xs), cuda(xe), cuda(img), g).cpu().numpy()
+    assert p[0] == 0.0 and p[1] == 0.0
+    assert fwd_err(p, p_or) <= FWD_TOL
+    plan = ops.jp_plan_create(cuda(xs), cuda(xe), g)
+    assert fwd_err(ops.jp_fwd(plan, cuda(img)).cpu().numpy(), p_or) <= FWD_TOL
+    # empty input
+    e = torch.zeros((0, 3), device="cuda")
+    assert ops.jp_fwd_lors(e, e, cuda(img), g).numel() == 0
+    plan0 = ops.jp_plan_create(e, e, g)
+    assert ops.jp_fwd(plan0, cuda(img)).numel() == 0
+    out = torch.zeros(g.shape, device="cuda")
+    ops.jp_back(plan0, torch.zeros(0, device="cuda"), out)
+    assert float(out.abs().sum()) == 0.0
+
+
+def test_batched_frames(ops, clinical_img, lm_events):
+    """Three frames (one of them empty) in one plan and one launch, frame f
+    reading image f; each frame equals the oracle on its own events."""
+    g = synth.GEOM_CLINICAL
+    tof = synth.TOF_CLINICAL
+    xs, xe, tb = lm_events
+    cuts = [0, 70_001, 70_001, 130_000]
+    imgs = np.stack([clinical_img, 0.5 * clinical_img[::-1].copy(), clinical_img ** 2])
+    ys = synth.uniform_values(cuts[-1], 7001)
+    plan = ops.jp_plan_create_batch(cuda(xs[:cuts[-1]]), cuda(xe[:cuts[-1]]), g, cuts,
+                                    tof_bin=cuda(tb[:cuts[-1]]), tof_bin_width=tof.bin_width)
+    p = ops.jp_fwd_tof_lm(plan, cuda(imgs), tof).cpu().numpy()
+    out = torch.zeros((3,) + g.shape, device="cuda")
+    ops.jp_back_tof_lm(plan, cuda(ys), tof, out)
+    out = out.cpu().numpy()
+    for f in range(3):
+        a, b = cuts[f], cuts[f + 1]
+        if a == b:
+            assert float(np.abs(out[f]).sum()) == 0.0
+            continue
+        p_or, amb = oracle.fwd(xs[a:b], xe[a:b], imgs[f], g, "tof_lm", tof, tof_bin=tb[a:b],
+                               threads=THREADS, amb_eps=AMB_EPS, return_amb=True)
+        assert fwd_err(p[a:b], p_or, amb) <= FWD_TOL
+        b_or = oracle.back(xs[a:b], xe[a:b], ys[a:b], g, "tof_lm", tof, tof_bin=tb[a:b], threads=THREADS)
+        assert rel_l2(out[f], b_or) <= BACK_TOL
+    # rebind the same plan with a different split (no allocation)
+    cuts2 = [0, 10_000, 130_000]
+    ops.jp_plan_rebind(plan, cuda(xs[:cuts2[-1]]), cuda(xe[:cuts2[-1]]), cuts2, tof_bin=cuda(tb[:cuts2[-1]]))
+    p2 = ops.jp_fwd_tof_lm(plan, cuda(imgs[:2]), tof).cpu().numpy()
+    p_or0 = oracle.fwd(xs[:10_000], xe[:10_000], imgs[0], g, "tof_lm", tof, tof_bin=tb[:10_000],
+                       threads=THREADS)
+    assert fwd_err(p2[:10_000], p_or0) <= 2 * FWD_TOL
+
+
+def test_osem_elementwise(ops):
+    rng = np.random.Generator(np.random.PCG64(8001))
+    p = rng.uniform(0, 5, size=100_003).astype(np.float32)
+    b = np.array([0.3, 1.1], np.float32)
+    q = ops.jp_osem_ratio(None, cuda(p), cuda(b[:1]), out=torch.empty(len(p), device="cuda"))
+    np.testing.assert_allclose(q.cpu().numpy(), 1.0 / (p.astype(np.float64) + 0.3), rtol=1e-6)
+    x = rng.uniform(0, 2, size=(2, 1000)).astype(np.float32)
+    bp = rng.uniform(0, 2, size=(2, 1000)).astype(np.float32)
+    s = rng.uniform(0, 2, size=1000).astype(np.float32)
+    s[::7] = 0
+    dx = cuda(x)
+    ops.jp_osem_update(dx, cuda(bp), cuda(s), 0.125, 1000, n_frames=2, img_stride=1000, s_stride=0)
+    ref = np.where(s > 0, x.astype(np.float64) * bp / (s.astype(np.float64) * 0.125), 0.0)
+    np.testing.assert_allclose(dx.cpu().numpy(), ref, rtol=2e-6)
+    v = rng.uniform(0, 1, size=1_000_001).astype(np.float32)
+    assert float(ops.jp_sum_f64(cuda(v))) == pytest.approx(float(v.astype(np.float64).sum()), rel=1e-12)
