@@ -86,17 +86,27 @@ typedef struct {
  * LORs of a warp walk nearly the same voxels (paper Sec. 4 suggests event
  * pre-sorting; Sec. 2.6 and 3 show the memory-order sensitivity it removes). */
 typedef struct {
-  int32_t block;          /* threads per CTA for projections (0 = 256; 64..1024, multiple of 32) */
-  int32_t slope_bins;     /* bins over the in-plane slope d_b/d_a in [-1,1] (0 = 64) */
-  int32_t offset_bins;    /* bins over the in-plane offset at the central plane (0 = 64) */
+  int32_t block;          /* threads per CTA for projections (0 = 256; 64..512, multiple of 32) */
+  int32_t slope_bins;     /* bins over the in-plane slope d_b/d_a in [-1,1] (0 = 128) */
+  int32_t offset_bins;    /* bins over the in-plane offset at the central plane (0 = 256) */
   int32_t window_bins;    /* bins over the TOF-window centre along the principal
-                             axis, listmode plans only (0 = 16) */
+                             axis, listmode plans only (0 = 64); n_frames * 3 * slope *
+                             offset * window must stay below 2^28 */
   float tof_bin_width;    /* mm; > 0 with tof_bin given: bin listmode events by
                              their TOF window centre; 0 = ignore */
-  int32_t flags;          /* JP_PLAN_KEEP_ORDER: no sorting (identity order) */
+  int32_t flags;          /* JP_PLAN_KEEP_ORDER: no sorting (identity order);
+                             JP_PLAN_TOF_EXACT: evaluate every TOF weight with erff
+                             instead of the interpolated table (see below) */
 } jp_plan_opts;
 
 #define JP_PLAN_KEEP_ORDER 1
+#define JP_PLAN_TOF_EXACT 2
+
+/* TOF weights in planned calls come by default from a table of the exact
+ * erf difference at JP_TOF_TABLE nodes over [-R, R] (R = n_sigmas*sigma +
+ * w/2) with linear interpolation (max relative deviation ~1e-6 of the peak
+ * weight for the clinical parameters); JP_PLAN_TOF_EXACT selects erff. */
+#define JP_TOF_TABLE 2048
 
 /*
  * jp_plan_create_batch -- sort and pack the LORs of n_frames frames.
@@ -109,7 +119,10 @@ typedef struct {
  *   g, opts            image grid (all frames share it); opts may be NULL
  * The plan allocates device memory for exactly n_total LORs and n_frames
  * frames (its capacity) and copies what it needs: the input arrays may be
- * freed once the stream has passed this call.  Frame f of a batched call
+ * freed once the stream has passed this call.  It also holds the projection
+ * workspace (per frame, a zero-padded 4-neighbour copy of the image for each
+ * principal axis: 16 * sum_a n_a (n_b+2)(n_c+2) bytes), so the projection
+ * calls allocate nothing.  Frame f of a batched call
  * reads/writes image f at `image + f * img_stride`.
  * Errors: JP_ERR_ARG, JP_ERR_ALIGN, JP_ERR_NOMEM, JP_ERR_CUDA.
  */

@@ -227,11 +227,38 @@ __device__ __forceinline__ float tof_g(float dist, const DevTof& t) {
 }
 
 // ---------------------------------------------------------------------------
-// plan
+// quad images: for principal axis a, Q_a[k][i][j] (k along a, i along b,
+// j along c, i and j from -1 to n_b / n_c) holds the 4 bilinear neighbours
+// (f(k,i,j), f(k,i+1,j), f(k,i,j+1), f(k,i+1,j+1)) with zeros outside the
+// grid, so a plane sample is one 16-byte load (forward) or one 16-byte
+// vector reduction (back projection) with no bounds tests.
 // ---------------------------------------------------------------------------
+struct QuadLayout {
+  int nb2[3], nc2[3];  // n_b + 2, n_c + 2 for axis a
+  int64_t plane[3];    // nb2 * nc2
+  int64_t base[3];     // float4 offset of Q_a inside one slot
+  int64_t slot;        // float4 per slot (one image)
+};
+
+inline QuadLayout quad_layout(const jp_image_geom& g) {
+  QuadLayout q;
+  int64_t off = 0;
+  for (int a = 0; a < 3; ++a) {
+    int b = (a == 0) ? 1 : 0, c = (a == 2) ? 1 : 2;
+    q.nb2[a] = g.n[b] + 2;
+    q.nc2[a] = g.n[c] + 2;
+    q.plane[a] = (int64_t)q.nb2[a] * q.nc2[a];
+    q.base[a] = off;
+    off += (int64_t)g.n[a] * q.plane[a];
+  }
+  q.slot = off;
+  return q;
+}
+
 struct PlanDims {
   int slope_bins, offset_bins, window_bins;
   int keys_per_frame;
+  int keys_per_axis;
 };
 
 }  // namespace jp
@@ -254,15 +281,8 @@ struct jp_plan_s {
   int64_t* frame_off_host;// pinned [frame_capacity + 1]
   int64_t hist_len;
   int64_t scan_blocks_cap;
+  // projection workspace
+  jp::QuadLayout ql;
+  float4* quads;          // [frame_capacity * ql.slot]
+  int32_t* axis_used;     // [frame_capacity * 3]: frame f has LORs with principal axis a
 };
-
-namespace jp {
-// binned-plan accessors for the projection kernels
-struct PlanView {
-  const float4* lor;
-  const int32_t* perm;
-  const int64_t* frame_off;
-  int n_frames;
-  int64_t n;
-};
-}  // namespace jp

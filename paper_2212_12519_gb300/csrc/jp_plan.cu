@@ -24,7 +24,7 @@ namespace jp {
 namespace {
 
 constexpr int kScanBlock = 1024;
-constexpr int kScanItems = 4;
+constexpr int kScanItems = 16;
 constexpr int kScanTile = kScanBlock * kScanItems;
 
 __device__ __forceinline__ int frame_of(const int64_t* __restrict__ off, int n_frames, int64_t i) {
@@ -191,6 +191,20 @@ __global__ void scatter_kernel(KeyParams p, const uint32_t* __restrict__ keys, u
   perm[pos] = (int32_t)j;
 }
 
+// Frame f has LORs with principal axis a iff its keys of axis a hold any LOR.
+// After the scatter, cursor[key] is the end offset of bin `key`.
+__global__ void axis_flags_kernel(const uint32_t* __restrict__ cursor, int n_frames, int keys_per_frame,
+                                  int keys_per_axis, int keep_order, int32_t* __restrict__ used) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_frames * 3) return;
+  if (keep_order) { used[t] = 1; return; }
+  int f = t / 3, a = t - 3 * f;
+  int64_t first = (int64_t)f * keys_per_frame + (int64_t)a * keys_per_axis;
+  int64_t last = first + keys_per_axis - 1;
+  uint32_t start = first > 0 ? cursor[first - 1] : 0u;
+  used[t] = cursor[last] > start ? 1 : 0;
+}
+
 int validate_offsets(const int64_t* off, int32_t n_frames, int64_t* n_total) {
   if (!off) return fail(JP_ERR_ARG, "frame_offsets is NULL");
   if (n_frames < 1) return fail(JP_ERR_ARG, "n_frames must be >= 1");
@@ -222,7 +236,10 @@ int bind(jp_plan p, const float* xs, const float* xe, const int16_t* tof_bin, co
                               cudaMemcpyHostToDevice, st));
   p->n = n;
   p->n_frames = n_frames;
-  if (n == 0) return JP_OK;
+  if (n == 0) {
+    JP_TRY_CUDA(cudaMemsetAsync(p->axis_used, 0, sizeof(int32_t) * 3 * n_frames, st));
+    return JP_OK;
+  }
   KeyParams kp;
   kp.xs = xs; kp.xe = xe; kp.tof_bin = tof_bin; kp.delta = delta; kp.n = n;
   kp.frame_off = p->frame_off_dev; kp.n_frames = n_frames; kp.g = g;
@@ -250,6 +267,10 @@ int bind(jp_plan p, const float* xs, const float* xe, const int16_t* tof_bin, co
   }
   scatter_kernel<<<blocks, 256, 0, st>>>(kp, p->keys, p->hist, p->lor, p->perm);
   count_launch();
+  axis_flags_kernel<<<(n_frames * 3 + 127) / 128, 128, 0, st>>>(p->hist, n_frames, p->dims.keys_per_frame,
+                                                               p->dims.keys_per_axis, kp.keep_order,
+                                                               p->axis_used);
+  count_launch();
   JP_TRY_CUDA(cudaGetLastError());
   return JP_OK;
 }
@@ -263,6 +284,8 @@ void free_plan(jp_plan p) {
   cudaFree(p->block_sums);
   cudaFree(p->frame_off_dev);
   cudaFreeHost(p->frame_off_host);
+  cudaFree(p->quads);
+  cudaFree(p->axis_used);
   delete p;
 }
 
@@ -290,17 +313,17 @@ extern "C" int jp_plan_create_batch(jp_plan* out, const float* xs, const float* 
   std::memset(&o, 0, sizeof(o));
   if (opts) o = *opts;
   if (o.block == 0) o.block = 256;
-  if (o.block < 64 || o.block > 1024 || (o.block % 32) != 0) return fail(JP_ERR_ARG, "opts.block must be 64..1024, multiple of 32");
-  if (o.slope_bins == 0) o.slope_bins = 64;
-  if (o.offset_bins == 0) o.offset_bins = 64;
-  if (o.window_bins == 0) o.window_bins = 16;
+  if (o.block < 64 || o.block > 512 || (o.block % 32) != 0) return fail(JP_ERR_ARG, "opts.block must be 64..512, multiple of 32");
+  if (o.slope_bins == 0) o.slope_bins = 128;
+  if (o.offset_bins == 0) o.offset_bins = 256;
+  if (o.window_bins == 0) o.window_bins = 64;
   if (o.slope_bins < 1 || o.offset_bins < 1 || o.window_bins < 1) return fail(JP_ERR_ARG, "bin counts must be >= 1");
   if (!(o.tof_bin_width >= 0.f) || !isfinite(o.tof_bin_width)) return fail(JP_ERR_ARG, "opts.tof_bin_width must be finite and >= 0");
   int window_bins = (o.tof_bin_width > 0.f && tof_bin) ? o.window_bins : 1;
   int64_t kpf = 3LL * o.slope_bins * o.offset_bins * window_bins;
   if (o.flags & JP_PLAN_KEEP_ORDER) kpf = 1;
   if (kpf * (int64_t)n_frames >= (int64_t)kScanTile * kScanTile)
-    return fail(JP_ERR_ARG, "too many bins (n_frames * 3 * slope * offset * window >= 2^24)");
+    return fail(JP_ERR_ARG, "too many bins (n_frames * 3 * slope * offset * window >= 2^28)");
   jp_plan p = new (std::nothrow) jp_plan_s();
   if (!p) return fail(JP_ERR_NOMEM, "host allocation failed");
   std::memset(p, 0, sizeof(*p));
@@ -312,6 +335,13 @@ extern "C" int jp_plan_create_batch(jp_plan* out, const float* xs, const float* 
   p->dims.offset_bins = o.offset_bins;
   p->dims.window_bins = window_bins;
   p->dims.keys_per_frame = (int)kpf;
+  p->dims.keys_per_axis = (o.flags & JP_PLAN_KEEP_ORDER) ? 1 : o.slope_bins * o.offset_bins * window_bins;
+  p->ql = quad_layout(*g);
+  for (int a = 0; a < 3; ++a)
+    if ((int64_t)g->n[a] * p->ql.plane[a] >= (int64_t)INT32_MAX) {
+      delete p;
+      return fail(JP_ERR_ARG, "padded image too large (>= 2^31 entries per axis)");
+    }
   p->has_tof_bin = tof_bin != nullptr;
   p->has_delta = delta != nullptr;
   p->hist_len = kpf * n_frames;
@@ -326,6 +356,8 @@ extern "C" int jp_plan_create_batch(jp_plan* out, const float* xs, const float* 
   if (e == cudaSuccess) e = cudaMalloc(&p->block_sums, sizeof(uint32_t) * (p->scan_blocks_cap + 1));
   if (e == cudaSuccess) e = cudaMalloc(&p->frame_off_dev, sizeof(int64_t) * (n_frames + 1));
   if (e == cudaSuccess) e = cudaMallocHost(&p->frame_off_host, sizeof(int64_t) * (n_frames + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&p->quads, sizeof(float4) * (size_t)p->ql.slot * (size_t)n_frames);
+  if (e == cudaSuccess) e = cudaMalloc(&p->axis_used, sizeof(int32_t) * 3 * (size_t)n_frames);
   if (e != cudaSuccess) {
     cudaGetLastError();
     free_plan(p);

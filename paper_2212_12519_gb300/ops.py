@@ -24,6 +24,7 @@ F32 = ctypes.c_float
 
 TOF_MODES = {"nontof": 0, "tof_sino": 1, "tof_lm": 2}
 JP_PLAN_KEEP_ORDER = 1
+JP_PLAN_TOF_EXACT = 2
 
 
 class JosephError(RuntimeError):
@@ -177,9 +178,11 @@ class Plan:
             pass
 
 
-def _opts(block=0, slope_bins=0, offset_bins=0, window_bins=0, tof_bin_width=0.0, keep_order=False):
+def _opts(block=0, slope_bins=0, offset_bins=0, window_bins=0, tof_bin_width=0.0, keep_order=False,
+          tof_exact=False):
+    flags = (JP_PLAN_KEEP_ORDER if keep_order else 0) | (JP_PLAN_TOF_EXACT if tof_exact else 0)
     return PlanOptsC(int(block), int(slope_bins), int(offset_bins), int(window_bins),
-                     float(tof_bin_width), JP_PLAN_KEEP_ORDER if keep_order else 0)
+                     float(tof_bin_width), flags)
 
 
 def jp_plan_create_batch(xs, xe, geom, frame_offsets, tof_bin=None, delta=None, stream=None,
