@@ -234,6 +234,13 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, W, plan, g, tof, dev, ws)
+    plan.destroy()
+    del W["xs"], W["xe"], W["tb"], W["w"], W["bvec"]
+    torch.cuda.empty_cache()
+    serving = None
+    if not args.no_serving and rank == 0:
+        rates = [float(r) for r in args.serving_rates.split(",")]
+        serving = run_serving(n_requests=args.serving_requests, rates=rates)
 
     if rank == 0:
         peaks, peak_kind = measured_peaks()
@@ -260,6 +267,7 @@ def run_ours(args):
             "clocks": clk,
             "gpu_launches": int(launches),
             "e2e": e2e,
+            "serving": serving,
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(W, g, tof, target_s=args.cpu_seconds)
@@ -308,6 +316,45 @@ def run_e2e(args, W, plan, g, tof, dev, ws):
     ms = t0.elapsed_time(t1) / n
     return {"value": W["xs"].shape[0] * ws / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
             "steps": n, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+
+# ---------------------------------------------------------------------------
+# served listmode OSEM (frame stream): batched vs sequential plain
+# ---------------------------------------------------------------------------
+def run_serving(n_requests=200, rates=(1.0,), pool_events=20_000_000, max_slots=8, budget_gb=None,
+                use_graphs=True, seed=5001):
+    from paper_2212_12519_gb300 import osem, serve, synth
+    tof = synth.TOF_CLINICAL
+    t0 = time.perf_counter()
+    pools = serve.make_event_pools(tof, pool_events=pool_events)
+    sens, checks = {}, {}
+    for shape, pool in pools.items():
+        sens[shape], checks[str(shape)] = osem.sensitivity(pool["geom"])
+    setup_s = time.perf_counter() - t0
+    geoms = [p["geom"] for p in pools.values()]
+    # mu_seq: sequential plain server, all requests available at once
+    reqs = serve.make_requests(pools, n_requests, rate=1e9, seed=seed)
+    seq = serve.OSEMServer(sens, tof, mode="sequential")
+    base = seq.run(reqs)
+    mu = base["frames_per_s"]
+    bat = serve.OSEMServer(sens, tof, mode="batched", max_slots=max_slots, use_graphs=use_graphs,
+                           hbm_budget=None if budget_gb is None else int(budget_gb * 2 ** 30))
+    bat.reserve(int(2e7), geoms)
+    serve.reset(reqs)
+    cap = bat.run(reqs)
+    out = {"requests": n_requests, "mu_seq_frames_per_s": mu, "batched_capacity_frames_per_s": cap["frames_per_s"],
+           "sensitivity_fp64_check": checks, "setup_s": setup_s, "sweep": []}
+    for f in rates:
+        lam = f * mu
+        reqs = serve.make_requests(pools, n_requests, rate=lam, seed=seed)
+        r_seq = seq.run(reqs)
+        serve.reset(reqs)
+        r_bat = bat.run(reqs)
+        out["sweep"].append({"rate_x_mu_seq": f, "rate_frames_per_s": lam,
+                             "sequential": {k: r_seq[k] for k in ("frames_per_s", "p50_ms", "p99_ms")},
+                             "batched": {k: r_bat[k] for k in ("frames_per_s", "p50_ms", "p99_ms", "events_per_s")}})
+    bat.close()
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -396,6 +443,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=200)
+    ap.add_argument("--serving-rates", default="1.0")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

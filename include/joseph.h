@@ -94,6 +94,9 @@ typedef struct {
                              offset * window must stay below 2^28 */
   float tof_bin_width;    /* mm; > 0 with tof_bin given: bin listmode events by
                              their TOF window centre; 0 = ignore */
+  int32_t lors_per_warp;  /* LORs a warp walks at once: 32 = one LOR per thread;
+                             1, 2 or 4 = 32, 16 or 8 lanes step through consecutive
+                             planes of one LOR (coalesced); 0 = per-mode default */
   int32_t flags;          /* JP_PLAN_KEEP_ORDER: no sorting (identity order);
                              JP_PLAN_TOF_EXACT: evaluate every TOF weight with erff
                              instead of the interpolated table (see below) */
@@ -101,6 +104,10 @@ typedef struct {
 
 #define JP_PLAN_KEEP_ORDER 1
 #define JP_PLAN_TOF_EXACT 2
+#define JP_PLAN_INTERLEAVED 4  /* frame of caller LOR j is j mod n_frames (listmode
+                                  OSEM subsets); frame_offsets then only give
+                                  offsets[n_frames] = n_total and all frames share
+                                  one image */
 
 /* TOF weights in planned calls come by default from a table of the exact
  * erf difference at JP_TOF_TABLE nodes over [-R, R] (R = n_sigmas*sigma +
@@ -202,6 +209,27 @@ int jp_osem_ratio(jp_plan p, const float* proj, const float* b, float* q, int64_
                   void* stream);
 int jp_osem_update(float* x, const float* bp, const float* sens, float scale, int64_t nvox,
                    int32_t n_frames, int64_t img_stride, int64_t s_stride, void* stream);
+
+/*
+ * jp_osem_subset_tof_lm -- the projection work of one listmode-OSEM subset
+ * update (paper Sec. 2.6 and 3, x <- x / s_sub * A_S^T (1 / (A_S x + b))),
+ * fused per event: forward projection of x, ratio 1/(p + b) and back
+ * projection of the ratio, for the events of frames [f0, f1) of a
+ * JP_PLAN_INTERLEAVED plan; then, per voxel,
+ *     x[j] <- sens[j] > 0 ? x[j] * bp[j] / (sens[j] * sens_scale) : 0
+ * where bp = A_S^T (1/(A_S x + b)) is held in the plan's workspace.
+ *   x          device float32 image (updated in place)
+ *   sens       device float32 sensitivity image A^T 1
+ *   sens_scale 1 / n_subsets in the paper's update
+ *   b          additive background (> = 0) of every event
+ * Errors: JP_ERR_ARG, JP_ERR_STATE (plan not interleaved or without TOF bins),
+ * JP_ERR_CUDA.
+ */
+int jp_osem_subset_tof_lm(jp_plan p, int32_t f0, int32_t f1, float* x, const float* sens,
+                          float sens_scale, float b, const jp_tof* t, void* stream);
+
+/* listmode OSEM start image: x[j] = sens[j] > 0 ? 1 : 0 for nvox voxels */
+int jp_osem_init(float* x, const float* sens, int64_t nvox, void* stream);
 
 /* FP64 sum of a float32 device array into *out (device double).  Used only
  * for the sensitivity-normalisation check sum_j (A^T 1)_j = sum_i (A 1)_i. */

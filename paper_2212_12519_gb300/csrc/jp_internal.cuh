@@ -133,6 +133,9 @@ __device__ __forceinline__ bool ray_setup(const float xs[3], const float xe[3],
   const float d0 = xe[0] - xs[0], d1 = xe[1] - xs[1], d2 = xe[2] - xs[2];
   const float L = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
   r.k0 = 1; r.k1 = 0;
+  r.a = 0; r.w0 = 0.f; r.kc = 0.f;
+  r.uc = r.du = r.wc = r.dw = r.tc = r.dt = 0.f;
+  r.sa = r.sb = r.sc = 0; r.nb = r.nc = 1;
   if (!(L > 0.f)) return false;
   const int a = principal_axis(xs, xe);
   const int b = (a == 0) ? 1 : 0;
@@ -227,15 +230,26 @@ __device__ __forceinline__ float tof_g(float dist, const DevTof& t) {
 }
 
 // ---------------------------------------------------------------------------
-// quad images: for principal axis a, Q_a[k][i][j] (k along a, i along b,
-// j along c, i and j from -1 to n_b / n_c) holds the 4 bilinear neighbours
-// (f(k,i,j), f(k,i+1,j), f(k,i,j+1), f(k,i+1,j+1)) with zeros outside the
-// grid, so a plane sample is one 16-byte load (forward) or one 16-byte
-// vector reduction (back projection) with no bounds tests.
+// quad images: for principal axis a, entry (i, j, k) -- k the plane along a,
+// i along b and j along c, i and j from -1 to n_b / n_c -- holds the 4
+// bilinear neighbours (f(k,i,j), f(k,i+1,j), f(k,i,j+1), f(k,i+1,j+1)) with
+// zeros outside the grid, so a plane sample is one 16-byte load (forward) or
+// one 16-byte vector reduction (back projection) with no bounds tests.  Two
+// orders are used:
+//   plane-major   index = (k * nb2 + (i + 1)) * nc2 + (j + 1): the lanes of a
+//                 warp following 32 neighbouring LORs (one per thread) read
+//                 nearby entries of the same plane rows;
+//   plane-fastest index = ((i + 1) * nc2 + (j + 1)) * n_a + k: the lanes of a
+//                 group walking consecutive planes of one LOR touch
+//                 consecutive 16-byte entries (coalesced reductions).
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ int quad_index(bool kfast, int k, int ip, int jp, int na, int nb2, int nc2) {
+  return kfast ? (ip * nc2 + jp) * na + k : (k * nb2 + ip) * nc2 + jp;
+}
+
 struct QuadLayout {
   int nb2[3], nc2[3];  // n_b + 2, n_c + 2 for axis a
-  int64_t plane[3];    // nb2 * nc2
+  int64_t size[3];     // n_a * nb2 * nc2 entries of Q_a
   int64_t base[3];     // float4 offset of Q_a inside one slot
   int64_t slot;        // float4 per slot (one image)
 };
@@ -247,9 +261,9 @@ inline QuadLayout quad_layout(const jp_image_geom& g) {
     int b = (a == 0) ? 1 : 0, c = (a == 2) ? 1 : 2;
     q.nb2[a] = g.n[b] + 2;
     q.nc2[a] = g.n[c] + 2;
-    q.plane[a] = (int64_t)q.nb2[a] * q.nc2[a];
+    q.size[a] = (int64_t)g.n[a] * q.nb2[a] * q.nc2[a];
     q.base[a] = off;
-    off += (int64_t)g.n[a] * q.plane[a];
+    off += q.size[a];
   }
   q.slot = off;
   return q;
@@ -283,6 +297,7 @@ struct jp_plan_s {
   int64_t scan_blocks_cap;
   // projection workspace
   jp::QuadLayout ql;
-  float4* quads;          // [frame_capacity * ql.slot]
+  float4* quads;          // [quad_slots * ql.slot]
+  int32_t quad_slots;     // frames with their own image, or 2 (image + back projection) when interleaved
   int32_t* axis_used;     // [frame_capacity * 3]: frame f has LORs with principal axis a
 };

@@ -42,6 +42,11 @@ __global__ void update_kernel(float* __restrict__ x, const float* __restrict__ b
   }
 }
 
+__global__ void init_kernel(float* __restrict__ x, const float* __restrict__ s, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = s[i] > 0.f ? 1.f : 0.f;
+}
+
 __global__ void sum_f64_kernel(const float* __restrict__ x, int64_t n, double* out) {
   __shared__ double red[32];
   double s = 0.0;
@@ -103,6 +108,17 @@ extern "C" int jp_osem_update(float* x, const float* bp, const float* s, float s
   if (total == 0) return JP_OK;
   update_kernel<<<grid_for(total, 256), 256, 0, (cudaStream_t)stream>>>(x, bp, s, scale, nvox, n_frames,
                                                                        stride, s_stride);
+  count_launch();
+  JP_TRY_CUDA(cudaGetLastError());
+  return JP_OK;
+}
+
+extern "C" int jp_osem_init(float* x, const float* s, int64_t n, void* stream) {
+  clear_error();
+  if (n < 0 || (n > 0 && (!x || !s))) return fail(JP_ERR_ARG, "bad arguments");
+  if (!aligned(x, 4) || !aligned(s, 4)) return fail(JP_ERR_ALIGN, "misaligned array");
+  if (n == 0) return JP_OK;
+  init_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(x, s, n);
   count_launch();
   JP_TRY_CUDA(cudaGetLastError());
   return JP_OK;

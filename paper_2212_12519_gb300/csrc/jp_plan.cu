@@ -48,6 +48,7 @@ struct KeyParams {
   int slope_bins, offset_bins, window_bins, keys_per_frame;
   float tof_width;  // > 0: listmode window binning
   int keep_order;
+  int interleaved;  // frame of LOR j is j mod n_frames
 };
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
@@ -55,7 +56,7 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? l
 __global__ void key_kernel(KeyParams p, uint32_t* __restrict__ keys, uint32_t* __restrict__ hist) {
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= p.n) return;
-  int f = frame_of(p.frame_off, p.n_frames, j);
+  int f = p.interleaved ? (int)(j % p.n_frames) : frame_of(p.frame_off, p.n_frames, j);
   uint32_t key = 0;
   if (!p.keep_order) {
     float xs[3] = {p.xs[3 * j], p.xs[3 * j + 1], p.xs[3 * j + 2]};
@@ -219,8 +220,16 @@ int validate_offsets(const int64_t* off, int32_t n_frames, int64_t* n_total) {
 int bind(jp_plan p, const float* xs, const float* xe, const int16_t* tof_bin, const float* delta,
          const int64_t* off, int32_t n_frames, cudaStream_t st) {
   int64_t n = 0;
-  int rc = validate_offsets(off, n_frames, &n);
-  if (rc) return rc;
+  const bool interleaved = (p->opts.flags & JP_PLAN_INTERLEAVED) != 0;
+  if (interleaved) {
+    if (!off || n_frames < 1) return fail(JP_ERR_ARG, "frame_offsets / n_frames");
+    n = off[n_frames];
+    if (n < 0 || n >= (int64_t)INT32_MAX) return fail(JP_ERR_ARG, "n_total must be in [0, 2^31)");
+  } else {
+    int rc0 = validate_offsets(off, n_frames, &n);
+    if (rc0) return rc0;
+  }
+  int rc = JP_OK;
   if (n > p->capacity || n_frames > p->frame_capacity)
     return fail(JP_ERR_ARG, "rebind exceeds the plan's capacity");
   if (n > 0 && (!xs || !xe)) return fail(JP_ERR_ARG, "xstart/xend is NULL");
@@ -231,7 +240,14 @@ int bind(jp_plan p, const float* xs, const float* xe, const int16_t* tof_bin, co
   DevGeom g;
   rc = make_geom(&p->g, &g);
   if (rc) return rc;
-  std::memcpy(p->frame_off_host, off, sizeof(int64_t) * (n_frames + 1));
+  if (interleaved) {
+    // frame f holds LORs f, f + n_frames, ...: its count is known up front
+    p->frame_off_host[0] = 0;
+    for (int32_t f = 0; f < n_frames; ++f)
+      p->frame_off_host[f + 1] = p->frame_off_host[f] + n / n_frames + (f < n % n_frames ? 1 : 0);
+  } else {
+    std::memcpy(p->frame_off_host, off, sizeof(int64_t) * (n_frames + 1));
+  }
   JP_TRY_CUDA(cudaMemcpyAsync(p->frame_off_dev, p->frame_off_host, sizeof(int64_t) * (n_frames + 1),
                               cudaMemcpyHostToDevice, st));
   p->n = n;
@@ -247,6 +263,8 @@ int bind(jp_plan p, const float* xs, const float* xe, const int16_t* tof_bin, co
   kp.window_bins = p->dims.window_bins; kp.keys_per_frame = p->dims.keys_per_frame;
   kp.tof_width = p->opts.tof_bin_width;
   kp.keep_order = (p->opts.flags & JP_PLAN_KEEP_ORDER) ? 1 : 0;
+  kp.interleaved = interleaved ? 1 : 0;
+  if (interleaved && kp.keep_order) return fail(JP_ERR_ARG, "JP_PLAN_INTERLEAVED needs sorting (not KEEP_ORDER)");
   int64_t hist_len = (int64_t)n_frames * p->dims.keys_per_frame;
   int blocks = (int)((n + 255) / 256);
   if (!kp.keep_order) {
@@ -307,8 +325,15 @@ extern "C" int jp_plan_create_batch(jp_plan* out, const float* xs, const float* 
   int rc = make_geom(g, &dg);
   if (rc) return rc;
   int64_t n = 0;
-  rc = validate_offsets(off, n_frames, &n);
-  if (rc) return rc;
+  const bool interleaved = opts && (opts->flags & JP_PLAN_INTERLEAVED);
+  if (interleaved) {
+    if (!off || n_frames < 1) return fail(JP_ERR_ARG, "frame_offsets / n_frames");
+    n = off[n_frames];
+    if (n < 0 || n >= (int64_t)INT32_MAX) return fail(JP_ERR_ARG, "n_total must be in [0, 2^31)");
+  } else {
+    rc = validate_offsets(off, n_frames, &n);
+    if (rc) return rc;
+  }
   jp_plan_opts o;
   std::memset(&o, 0, sizeof(o));
   if (opts) o = *opts;
@@ -318,6 +343,9 @@ extern "C" int jp_plan_create_batch(jp_plan* out, const float* xs, const float* 
   if (o.offset_bins == 0) o.offset_bins = 256;
   if (o.window_bins == 0) o.window_bins = 64;
   if (o.slope_bins < 1 || o.offset_bins < 1 || o.window_bins < 1) return fail(JP_ERR_ARG, "bin counts must be >= 1");
+  if (o.lors_per_warp != 0 && o.lors_per_warp != 1 && o.lors_per_warp != 2 && o.lors_per_warp != 4 &&
+      o.lors_per_warp != 32)
+    return fail(JP_ERR_ARG, "opts.lors_per_warp must be 0, 1, 2, 4 or 32");
   if (!(o.tof_bin_width >= 0.f) || !isfinite(o.tof_bin_width)) return fail(JP_ERR_ARG, "opts.tof_bin_width must be finite and >= 0");
   int window_bins = (o.tof_bin_width > 0.f && tof_bin) ? o.window_bins : 1;
   int64_t kpf = 3LL * o.slope_bins * o.offset_bins * window_bins;
@@ -338,7 +366,7 @@ extern "C" int jp_plan_create_batch(jp_plan* out, const float* xs, const float* 
   p->dims.keys_per_axis = (o.flags & JP_PLAN_KEEP_ORDER) ? 1 : o.slope_bins * o.offset_bins * window_bins;
   p->ql = quad_layout(*g);
   for (int a = 0; a < 3; ++a)
-    if ((int64_t)g->n[a] * p->ql.plane[a] >= (int64_t)INT32_MAX) {
+    if (p->ql.size[a] >= (int64_t)INT32_MAX) {
       delete p;
       return fail(JP_ERR_ARG, "padded image too large (>= 2^31 entries per axis)");
     }
@@ -356,7 +384,8 @@ extern "C" int jp_plan_create_batch(jp_plan* out, const float* xs, const float* 
   if (e == cudaSuccess) e = cudaMalloc(&p->block_sums, sizeof(uint32_t) * (p->scan_blocks_cap + 1));
   if (e == cudaSuccess) e = cudaMalloc(&p->frame_off_dev, sizeof(int64_t) * (n_frames + 1));
   if (e == cudaSuccess) e = cudaMallocHost(&p->frame_off_host, sizeof(int64_t) * (n_frames + 1));
-  if (e == cudaSuccess) e = cudaMalloc(&p->quads, sizeof(float4) * (size_t)p->ql.slot * (size_t)n_frames);
+  p->quad_slots = interleaved ? 2 : std::max<int32_t>(n_frames, 1);
+  if (e == cudaSuccess) e = cudaMalloc(&p->quads, sizeof(float4) * (size_t)p->ql.slot * (size_t)p->quad_slots);
   if (e == cudaSuccess) e = cudaMalloc(&p->axis_used, sizeof(int32_t) * 3 * (size_t)n_frames);
   if (e != cudaSuccess) {
     cudaGetLastError();

@@ -92,6 +92,12 @@ struct ProjParams {
   QuadLayout ql;
   const int32_t* axis_used;
   int shared;  // all frames use one image (img_stride == 0)
+  int kfast;   // quad order: 1 plane-fastest, 0 plane-major
+  // listmode OSEM subset update
+  float4* quads_bp;   // back-projection quads (plane-fastest)
+  float bg;           // additive background b
+  const float* sens;  // sensitivity image
+  float sens_scale;
 };
 
 __device__ __forceinline__ int frame_of(const int64_t* __restrict__ off, int n_frames, int64_t i) {
@@ -131,6 +137,13 @@ template <bool LUT>
 __device__ __forceinline__ float tof_weight(const float2* lut, float dist, const DevTof& T, float inv_h) {
   if (LUT) return lut_g(lut, dist, T.R, inv_h);
   return tof_g(dist, T);
+}
+
+__device__ __forceinline__ bool slot_axis_used(const int32_t* used, int slot, int a, int shared, int n_frames) {
+  if (!shared) return __ldg(used + 3 * slot + a) != 0;
+  for (int f = 0; f < n_frames; ++f)
+    if (__ldg(used + 3 * f + a)) return true;
+  return false;
 }
 
 // ---------------------------------------------------------------------------
@@ -175,7 +188,8 @@ __global__ void __launch_bounds__(kMaxBlock) planned_kernel(const ProjParams p) 
     }
     const int a = r.a;
     const int nc2 = sel3(a, p.ql.nc2[0], p.ql.nc2[1], p.ql.nc2[2]);
-    const int plane = (int)sel3(a, p.ql.plane[0], p.ql.plane[1], p.ql.plane[2]);
+    const int nb2 = sel3(a, p.ql.nb2[0], p.ql.nb2[1], p.ql.nb2[2]);
+    const int na = sel3(a, p.g.n[0], p.g.n[1], p.g.n[2]);
     const int64_t qoff = (int64_t)slot * p.ql.slot + sel3(a, p.ql.base[0], p.ql.base[1], p.ql.base[2]);
     const float ub = (float)r.nb, wb = (float)r.nc;
 
@@ -192,7 +206,7 @@ __global__ void __launch_bounds__(kMaxBlock) planned_kernel(const ProjParams p) 
           const float w = fminf(fmaxf(fmaf(kk, r.dw, r.wc), -1.f), wb);
           const float fu = floorf(u), fw = floorf(w);
           const float al = u - fu, be = w - fw;
-          const float4 v = __ldg(Q + (k * plane + ((int)fu + 1) * nc2 + ((int)fw + 1)));
+          const float4 v = __ldg(Q + quad_index(p.kfast, k, (int)fu + 1, (int)fw + 1, na, nb2, nc2));
           const float top = fmaf(be, v.z - v.x, v.x);
           const float bot = fmaf(be, v.w - v.y, v.y);
           const float s = fmaf(al, bot - top, top);
@@ -286,7 +300,7 @@ __global__ void __launch_bounds__(kMaxBlock) planned_kernel(const ProjParams p) 
         const float fu = floorf(u), fw = floorf(w);
         const float al = u - fu, be = w - fw;
         const float ca = (1.f - al) * coef, cb = al * coef;
-        atomicAdd(Q + (k * plane + ((int)fu + 1) * nc2 + ((int)fw + 1)),
+        atomicAdd(Q + quad_index(p.kfast, k, (int)fu + 1, (int)fw + 1, na, nb2, nc2),
                   make_float4(ca * (1.f - be), cb * (1.f - be), ca * be, cb * be));
       }
     }
@@ -294,14 +308,264 @@ __global__ void __launch_bounds__(kMaxBlock) planned_kernel(const ProjParams p) 
 }
 
 // ---------------------------------------------------------------------------
+// planned projection, G lanes per LOR (non-TOF and TOF listmode).  Each warp
+// takes 32 binned LORs; every lane sets up one of them, then the warp walks
+// them 32/G at a time: the setup is broadcast by shuffles and the G lanes of
+// a group step through consecutive planes (k = k0 + lane, k0 + lane + G, ...),
+// so their quad loads / reductions touch consecutive 16-byte entries.
+// ---------------------------------------------------------------------------
+template <int G>
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int MODE, bool BACK, bool LUT, int G>
+__global__ void __launch_bounds__(kMaxBlock) group_kernel(const ProjParams p) {
+  static_assert(MODE == 0 || MODE == 2, "group kernel: non-TOF or TOF listmode");
+  constexpr int E = 32 / G;  // LORs walked at once per warp
+  extern __shared__ float4 smem4[];
+  float2* lut = reinterpret_cast<float2*>(smem4);
+  const DevTof& T = p.tof;
+  if (MODE == 2 && LUT) {
+    build_lut(lut, T);
+    __syncthreads();
+  }
+  const float inv_h = (MODE == 2) ? (float)(kLut - 1) / (2.f * T.R) : 0.f;
+  const int lane = threadIdx.x & 31;
+  const int grp = lane / G, gl = lane - grp * G;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = warp * 32; base < p.n; base += nwarps * 32) {
+    // ---- per-lane setup of LOR base + lane ----
+    const int64_t i = base + lane;
+    Ray r;
+    r.k0 = 1; r.k1 = 0;
+    float d0 = 0.f, val = 0.f;
+    int slot = 0;
+    int32_t j = 0;
+    if (i < p.n) {
+      const float4 A = __ldg(p.lor + 2 * i);
+      const float4 B = __ldg(p.lor + 2 * i + 1);
+      const float xs[3] = {A.x, A.y, A.z};
+      const float xe[3] = {B.x, B.y, B.z};
+      j = __ldg(p.perm + i);
+      const int f = (p.n_frames > 1) ? frame_of(p.frame_off, p.n_frames, i) : 0;
+      slot = p.shared ? 0 : f;
+      bool live = ray_setup(xs, xe, p.g, r);
+      if (MODE == 2 && live) {
+        const float c = (float)__float_as_int(B.w) * T.width + A.w;
+        d0 = r.tc - c;
+        const float t1 = (-T.R - d0) / r.dt, t2 = (T.R - d0) / r.dt;
+        const float lo = fmaxf(ceilf(r.kc + fminf(t1, t2)), (float)r.k0);
+        const float hi = fminf(floorf(r.kc + fmaxf(t1, t2)), (float)r.k1);
+        r.k0 = (int)lo;
+        r.k1 = (int)hi;
+        live = lo <= hi;
+      }
+      if (BACK && live) {
+        val = r.w0 * __ldg(p.proj_in + j);
+        live = val != 0.f;
+      }
+      if (!live) { r.k0 = 1; r.k1 = 0; r.w0 = 0.f; val = 0.f; }
+    } else {
+      r.a = 0; r.kc = 0.f; r.uc = r.du = r.wc = r.dw = r.tc = r.dt = r.w0 = 0.f;
+    }
+    // ---- walk the 32 LORs, E at a time ----
+#pragma unroll 1
+    for (int pass = 0; pass < G; ++pass) {
+      const int src = pass * E + grp;
+      const int k0 = __shfl_sync(0xffffffffu, r.k0, src);
+      const int k1 = __shfl_sync(0xffffffffu, r.k1, src);
+      const int a = __shfl_sync(0xffffffffu, r.a, src);
+      const int sl = __shfl_sync(0xffffffffu, slot, src);
+      const int32_t jj = __shfl_sync(0xffffffffu, j, src);
+      const float uc = __shfl_sync(0xffffffffu, r.uc, src);
+      const float du = __shfl_sync(0xffffffffu, r.du, src);
+      const float wc = __shfl_sync(0xffffffffu, r.wc, src);
+      const float dw = __shfl_sync(0xffffffffu, r.dw, src);
+      const float w0 = __shfl_sync(0xffffffffu, BACK ? val : r.w0, src);
+      float dd0 = 0.f, ddt = 0.f;
+      if (MODE == 2) {
+        dd0 = __shfl_sync(0xffffffffu, d0, src);
+        ddt = __shfl_sync(0xffffffffu, r.dt, src);
+      }
+      const int na = sel3(a, p.g.n[0], p.g.n[1], p.g.n[2]);
+      const int nb = (a == 0) ? p.g.n[1] : p.g.n[0];
+      const int nc = (a == 2) ? p.g.n[1] : p.g.n[2];
+      const int nc2 = nc + 2;
+      const float kc = 0.5f * (float)(na - 1);
+      const float ub = (float)nb, wb = (float)nc;
+      const int64_t qoff = (int64_t)sl * p.ql.slot + sel3(a, p.ql.base[0], p.ql.base[1], p.ql.base[2]);
+      float sum = 0.f;
+      if (!BACK) {
+        const float4* __restrict__ Qa = p.quads + qoff;
+        for (int k = k0 + gl; k <= k1; k += G) {
+          const float kk = (float)k - kc;
+          const float u = fminf(fmaxf(fmaf(kk, du, uc), -1.f), ub);
+          const float w = fminf(fmaxf(fmaf(kk, dw, wc), -1.f), wb);
+          const float fu = floorf(u), fw = floorf(w);
+          const float al = u - fu, be = w - fw;
+          const float4 v = __ldg(Qa + (((int)fu + 1) * nc2 + ((int)fw + 1)) * na + k);
+          const float top = fmaf(be, v.z - v.x, v.x);
+          const float bot = fmaf(be, v.w - v.y, v.y);
+          const float s = fmaf(al, bot - top, top);
+          if (MODE == 0) sum += s;
+          else sum = fmaf(tof_weight<LUT>(lut, fmaf(kk, ddt, dd0), T, inv_h), s, sum);
+        }
+      }
+      for (int k = k0 + gl; BACK && k <= k1; k += G) {
+        const float kk = (float)k - kc;
+        const float u = fminf(fmaxf(fmaf(kk, du, uc), -1.f), ub);
+        const float w = fminf(fmaxf(fmaf(kk, dw, wc), -1.f), wb);
+        const float fu = floorf(u), fw = floorf(w);
+        const float al = u - fu, be = w - fw;
+        const int q = (((int)fu + 1) * nc2 + ((int)fw + 1)) * na + k;
+        {
+          float coef = w0;
+          if (MODE == 2) coef *= tof_weight<LUT>(lut, fmaf(kk, ddt, dd0), T, inv_h);
+          const float ca = (1.f - al) * coef, cb = al * coef;
+          atomicAdd(p.quads + qoff + q, make_float4(ca * (1.f - be), cb * (1.f - be), ca * be, cb * be));
+        }
+      }
+      if (!BACK) {
+        sum = group_sum<G>(sum);
+        if (gl == 0 && base + src < p.n) p.proj_out[jj] = w0 * sum;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// listmode OSEM subset kernel: per event, forward projection of x (quads in
+// p.quads), ratio 1 / (p + b), back projection of the ratio into p.quads_bp.
+// G lanes per event as in group_kernel; both quad sets are plane-fastest.
+// ---------------------------------------------------------------------------
+template <bool LUT, int G>
+__global__ void __launch_bounds__(kMaxBlock) osem_kernel(const ProjParams p) {
+  constexpr int E = 32 / G;
+  extern __shared__ float4 smem4[];
+  float2* lut = reinterpret_cast<float2*>(smem4);
+  const DevTof& T = p.tof;
+  if (LUT) {
+    build_lut(lut, T);
+    __syncthreads();
+  }
+  const float inv_h = (float)(kLut - 1) / (2.f * T.R);
+  const int lane = threadIdx.x & 31;
+  const int grp = lane / G, gl = lane - grp * G;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = warp * 32; base < p.n; base += nwarps * 32) {
+    const int64_t i = base + lane;
+    Ray r;
+    r.k0 = 1; r.k1 = 0;
+    float d0 = 0.f;
+    if (i < p.n) {
+      const float4 A = __ldg(p.lor + 2 * i);
+      const float4 B = __ldg(p.lor + 2 * i + 1);
+      const float xs[3] = {A.x, A.y, A.z};
+      const float xe[3] = {B.x, B.y, B.z};
+      bool live = ray_setup(xs, xe, p.g, r);
+      if (live) {
+        const float c = (float)__float_as_int(B.w) * T.width + A.w;
+        d0 = r.tc - c;
+        const float t1 = (-T.R - d0) / r.dt, t2 = (T.R - d0) / r.dt;
+        const float lo = fmaxf(ceilf(r.kc + fminf(t1, t2)), (float)r.k0);
+        const float hi = fminf(floorf(r.kc + fmaxf(t1, t2)), (float)r.k1);
+        r.k0 = (int)lo;
+        r.k1 = (int)hi;
+        live = lo <= hi;
+      }
+      if (!live) { r.k0 = 1; r.k1 = 0; r.w0 = 0.f; }
+    } else {
+      r.a = 0; r.uc = r.du = r.wc = r.dw = r.tc = r.dt = r.w0 = 0.f;
+    }
+#pragma unroll 1
+    for (int pass = 0; pass < G; ++pass) {
+      const int src = pass * E + grp;
+      const int k0 = __shfl_sync(0xffffffffu, r.k0, src);
+      const int k1 = __shfl_sync(0xffffffffu, r.k1, src);
+      const int a = __shfl_sync(0xffffffffu, r.a, src);
+      const float uc = __shfl_sync(0xffffffffu, r.uc, src);
+      const float du = __shfl_sync(0xffffffffu, r.du, src);
+      const float wc = __shfl_sync(0xffffffffu, r.wc, src);
+      const float dw = __shfl_sync(0xffffffffu, r.dw, src);
+      const float w0 = __shfl_sync(0xffffffffu, r.w0, src);
+      const float dd0 = __shfl_sync(0xffffffffu, d0, src);
+      const float ddt = __shfl_sync(0xffffffffu, r.dt, src);
+      const int na = sel3(a, p.g.n[0], p.g.n[1], p.g.n[2]);
+      const int nb = (a == 0) ? p.g.n[1] : p.g.n[0];
+      const int nc = (a == 2) ? p.g.n[1] : p.g.n[2];
+      const int nc2 = nc + 2;
+      const float kc = 0.5f * (float)(na - 1);
+      const float ub = (float)nb, wb = (float)nc;
+      const int64_t qoff = sel3(a, p.ql.base[0], p.ql.base[1], p.ql.base[2]);
+      // forward
+      float sum = 0.f;
+      for (int k = k0 + gl; k <= k1; k += G) {
+        const float kk = (float)k - kc;
+        const float u = fminf(fmaxf(fmaf(kk, du, uc), -1.f), ub);
+        const float w = fminf(fmaxf(fmaf(kk, dw, wc), -1.f), wb);
+        const float fu = floorf(u), fw = floorf(w);
+        const float al = u - fu, be = w - fw;
+        const float4 v = __ldg(p.quads + qoff + (((int)fu + 1) * nc2 + ((int)fw + 1)) * na + k);
+        const float top = fmaf(be, v.z - v.x, v.x);
+        const float bot = fmaf(be, v.w - v.y, v.y);
+        sum = fmaf(tof_weight<LUT>(lut, fmaf(kk, ddt, dd0), T, inv_h), fmaf(al, bot - top, top), sum);
+      }
+      sum = group_sum<G>(sum);
+      // ratio and back projection of it
+      const float coef0 = (k0 <= k1) ? w0 / fmaf(w0, sum, p.bg) : 0.f;
+      for (int k = k0 + gl; k <= k1 && coef0 != 0.f; k += G) {
+        const float kk = (float)k - kc;
+        const float u = fminf(fmaxf(fmaf(kk, du, uc), -1.f), ub);
+        const float w = fminf(fmaxf(fmaf(kk, dw, wc), -1.f), wb);
+        const float fu = floorf(u), fw = floorf(w);
+        const float al = u - fu, be = w - fw;
+        const float coef = coef0 * tof_weight<LUT>(lut, fmaf(kk, ddt, dd0), T, inv_h);
+        const float ca = (1.f - al) * coef, cb = al * coef;
+        atomicAdd(p.quads_bp + qoff + (((int)fu + 1) * nc2 + ((int)fw + 1)) * na + k,
+                  make_float4(ca * (1.f - be), cb * (1.f - be), ca * be, cb * be));
+      }
+    }
+  }
+}
+
+// x[v] <- s[v] > 0 ? x[v] * bp[v] / (s[v] * scale) : 0, with bp folded from
+// the back-projection quads (p.quads_bp, plane-fastest)
+__global__ void osem_update_kernel(const ProjParams p, float* __restrict__ x) {
+  const int32_t* used = p.axis_used;
+  bool use[3];
+  for (int a = 0; a < 3; ++a) use[a] = slot_axis_used(used, 0, a, 1, p.n_frames);
+  const DevGeom& g = p.g;
+  const int64_t nvox = (int64_t)g.n[0] * g.n[1] * g.n[2];
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvox; v += (int64_t)gridDim.x * blockDim.x) {
+    const int i0 = (int)(v / g.stride[0]);
+    const int r0 = (int)(v - (int64_t)i0 * g.stride[0]);
+    const int i1 = r0 / g.n[2], i2 = r0 - (r0 / g.n[2]) * g.n[2];
+    float bp = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (!use[a]) continue;
+      const int k = (a == 0) ? i0 : (a == 1 ? i1 : i2);
+      const int I = (a == 0) ? i1 : i0;
+      const int J = (a == 2) ? i1 : i2;
+      const int nc2 = p.ql.nc2[a], nb2 = p.ql.nb2[a];
+      const int na = g.n[a];
+      const float4* Q = p.quads_bp + p.ql.base[a];
+      bp += Q[quad_index(true, k, I + 1, J + 1, na, nb2, nc2)].x + Q[quad_index(true, k, I, J + 1, na, nb2, nc2)].y +
+            Q[quad_index(true, k, I + 1, J, na, nb2, nc2)].z + Q[quad_index(true, k, I, J, na, nb2, nc2)].w;
+    }
+    const float sv = p.sens[v] * p.sens_scale;
+    x[v] = sv > 0.f ? x[v] * bp / sv : 0.f;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // quad image build / clear / fold-back
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool slot_axis_used(const int32_t* used, int slot, int a, int shared, int n_frames) {
-  if (!shared) return __ldg(used + 3 * slot + a) != 0;
-  for (int f = 0; f < n_frames; ++f)
-    if (__ldg(used + 3 * f + a)) return true;
-  return false;
-}
 
 __global__ void quad_build_kernel(const ProjParams p) {
   const int slot = blockIdx.y / 3, a = blockIdx.y - 3 * (blockIdx.y / 3);
@@ -314,14 +578,23 @@ __global__ void quad_build_kernel(const ProjParams p) {
   const int sb = sel3(b, g.stride[0], g.stride[1], g.stride[2]);
   const int sc = sel3(c, g.stride[0], g.stride[1], g.stride[2]);
   const int nc2 = nc + 2;
-  const int64_t plane = (int64_t)(nb + 2) * nc2;
-  const int64_t total = (int64_t)na * plane;
+  const int64_t total = sel3(a, p.ql.size[0], p.ql.size[1], p.ql.size[2]);
   const float* __restrict__ im = p.img_in + (int64_t)slot * p.img_stride;
   float4* Q = p.quads + (int64_t)slot * p.ql.slot + sel3(a, p.ql.base[0], p.ql.base[1], p.ql.base[2]);
+  const int nb2 = nb + 2;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int k = (int)(e / plane);
-    const int rem = (int)(e - (int64_t)k * plane);
-    const int i = rem / nc2 - 1, jj = rem - (rem / nc2) * nc2 - 1;
+    int k, i, jj;
+    if (p.kfast) {
+      const int t = (int)(e / na);
+      k = (int)(e - (int64_t)t * na);
+      i = t / nc2 - 1;
+      jj = t - (t / nc2) * nc2 - 1;
+    } else {
+      const int t = (int)(e / nc2);
+      jj = (int)(e - (int64_t)t * nc2) - 1;
+      k = t / nb2;
+      i = t - k * nb2 - 1;
+    }
     const bool i0 = (unsigned)i < (unsigned)nb, i1 = (unsigned)(i + 1) < (unsigned)nb;
     const bool j0 = (unsigned)jj < (unsigned)nc, j1 = (unsigned)(jj + 1) < (unsigned)nc;
     const int64_t base = (int64_t)k * sa + (int64_t)i * sb + (int64_t)jj * sc;
@@ -337,8 +610,7 @@ __global__ void quad_build_kernel(const ProjParams p) {
 __global__ void quad_zero_kernel(const ProjParams p) {
   const int slot = blockIdx.y / 3, a = blockIdx.y - 3 * (blockIdx.y / 3);
   if (!slot_axis_used(p.axis_used, slot, a, p.shared, p.n_frames)) return;
-  const int64_t total = (int64_t)sel3(a, p.g.n[0], p.g.n[1], p.g.n[2]) *
-                        sel3(a, p.ql.plane[0], p.ql.plane[1], p.ql.plane[2]);
+  const int64_t total = sel3(a, p.ql.size[0], p.ql.size[1], p.ql.size[2]);
   float4* Q = p.quads + (int64_t)slot * p.ql.slot + sel3(a, p.ql.base[0], p.ql.base[1], p.ql.base[2]);
   const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
@@ -366,10 +638,13 @@ __global__ void quad_reduce_kernel(const ProjParams p) {
       const int k = (a == 0) ? i0 : (a == 1 ? i1 : i2);
       const int I = (a == 0) ? i1 : i0;                 // index along b
       const int J = (a == 2) ? i1 : i2;                 // index along c
-      const int nc2 = p.ql.nc2[a];
-      const float4* Q = Qs + p.ql.base[a] + (int64_t)k * p.ql.plane[a];
+      const int nc2 = p.ql.nc2[a], nb2 = p.ql.nb2[a];
+      const int na = g.n[a];
+      const float4* Q = Qs + p.ql.base[a];
+      const bool kf = p.kfast;
       // padded positions: voxel I sits at I + 1
-      s += Q[(I + 1) * nc2 + (J + 1)].x + Q[I * nc2 + (J + 1)].y + Q[(I + 1) * nc2 + J].z + Q[I * nc2 + J].w;
+      s += Q[quad_index(kf, k, I + 1, J + 1, na, nb2, nc2)].x + Q[quad_index(kf, k, I, J + 1, na, nb2, nc2)].y +
+           Q[quad_index(kf, k, I + 1, J, na, nb2, nc2)].z + Q[quad_index(kf, k, I, J, na, nb2, nc2)].w;
     }
     im[v] += s;
   }
@@ -533,6 +808,33 @@ int launch_planned(const ProjParams& p, int block, cudaStream_t st) {
   return JP_OK;
 }
 
+template <int MODE, bool BACK, bool LUT, int G>
+int launch_group(const ProjParams& p, int block, cudaStream_t st) {
+  auto kern = group_kernel<MODE, BACK, LUT, G>;
+  const size_t smem = (MODE == 2 && LUT) ? kLut * sizeof(float2) : 0;
+  int per_sm = 0;
+  JP_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem));
+  if (per_sm < 1) per_sm = 1;
+  int64_t need = (p.n + block - 1) / block;
+  int64_t grid = (int64_t)sm_count() * per_sm;
+  if (grid > need) grid = need;
+  if (grid < 1) grid = 1;
+  kern<<<(unsigned)grid, block, smem, st>>>(p);
+  count_launch();
+  JP_TRY_CUDA(cudaGetLastError());
+  return JP_OK;
+}
+
+template <int MODE, bool BACK, bool LUT>
+int launch_group_lpw(const ProjParams& p, int block, int lpw, cudaStream_t st) {
+  switch (lpw) {
+    case 1: return launch_group<MODE, BACK, LUT, 32>(p, block, st);
+    case 2: return launch_group<MODE, BACK, LUT, 16>(p, block, st);
+    case 4: return launch_group<MODE, BACK, LUT, 8>(p, block, st);
+    default: return launch_planned<MODE, BACK, LUT>(p, block, st);
+  }
+}
+
 template <int MODE, bool BACK>
 int launch_direct(const ProjParams& p, int block, cudaStream_t st) {
   if (p.n == 0) return JP_OK;
@@ -569,6 +871,8 @@ int planned(jp_plan pl, int mode, bool back, const float* in, float* out, int64_
   if (rc) return rc;
   if (img_stride != 0 && pl->n_frames > 1 && img_stride < (int64_t)p.g.n[0] * p.g.n[1] * p.g.n[2])
     return fail(JP_ERR_ARG, "img_stride smaller than one image");
+  if ((pl->opts.flags & JP_PLAN_INTERLEAVED) && img_stride != 0)
+    return fail(JP_ERR_ARG, "frames of an interleaved plan share one image (img_stride must be 0)");
   if (mode != 0) {
     rc = make_tof(t, mode == 1, &p.tof);
     if (rc) return rc;
@@ -592,8 +896,11 @@ int planned(jp_plan pl, int mode, bool back, const float* in, float* out, int64_
   const bool lut = (mode != 0) && !(pl->opts.flags & JP_PLAN_TOF_EXACT);
   const int block = pick_block(pl->opts.block, mode, p.tof, lut);
   cudaStream_t st = (cudaStream_t)stream;
-  const int64_t max_quad = std::max(std::max((int64_t)p.g.n[0] * p.ql.plane[0], (int64_t)p.g.n[1] * p.ql.plane[1]),
-                                    (int64_t)p.g.n[2] * p.ql.plane[2]);
+  const int64_t max_quad = std::max(std::max(p.ql.size[0], p.ql.size[1]), p.ql.size[2]);
+  int lpw = pl->opts.lors_per_warp;
+  if (lpw == 0) lpw = (mode == 1 || !back) ? 32 : 4;
+  if (mode == 1) lpw = 32;
+  p.kfast = (lpw == 32) ? 0 : 1;
   dim3 qgrid(aux_grid(max_quad, 256), slots * 3);
   if (!back) {
     quad_build_kernel<<<qgrid, 256, 0, st>>>(p);
@@ -603,16 +910,16 @@ int planned(jp_plan pl, int mode, bool back, const float* in, float* out, int64_
   count_launch();
   JP_TRY_CUDA(cudaGetLastError());
   switch (mode * 4 + (back ? 2 : 0) + (lut ? 1 : 0)) {
-    case 0: rc = launch_planned<0, false, false>(p, block, st); break;
-    case 2: rc = launch_planned<0, true, false>(p, block, st); break;
+    case 0: rc = launch_group_lpw<0, false, false>(p, block, lpw, st); break;
+    case 2: rc = launch_group_lpw<0, true, false>(p, block, lpw, st); break;
     case 4: rc = launch_planned<1, false, false>(p, block, st); break;
     case 5: rc = launch_planned<1, false, true>(p, block, st); break;
     case 6: rc = launch_planned<1, true, false>(p, block, st); break;
     case 7: rc = launch_planned<1, true, true>(p, block, st); break;
-    case 8: rc = launch_planned<2, false, false>(p, block, st); break;
-    case 9: rc = launch_planned<2, false, true>(p, block, st); break;
-    case 10: rc = launch_planned<2, true, false>(p, block, st); break;
-    case 11: rc = launch_planned<2, true, true>(p, block, st); break;
+    case 8: rc = launch_group_lpw<2, false, false>(p, block, lpw, st); break;
+    case 9: rc = launch_group_lpw<2, false, true>(p, block, lpw, st); break;
+    case 10: rc = launch_group_lpw<2, true, false>(p, block, lpw, st); break;
+    case 11: rc = launch_group_lpw<2, true, true>(p, block, lpw, st); break;
     default: return fail(JP_ERR_ARG, "bad mode");
   }
   if (rc) return rc;
@@ -716,6 +1023,79 @@ extern "C" int jp_count_samples(jp_plan pl, int32_t mode, const jp_tof* t, uint6
   unsigned blocks = (unsigned)((p.n + 255) / 256);
   if (mode == 0) count_kernel<0><<<blocks, 256, 0, st>>>(p, (unsigned long long*)out);
   else count_kernel<2><<<blocks, 256, 0, st>>>(p, (unsigned long long*)out);
+  count_launch();
+  JP_TRY_CUDA(cudaGetLastError());
+  return JP_OK;
+}
+
+extern "C" int jp_osem_subset_tof_lm(jp_plan pl, int32_t f0, int32_t f1, float* x, const float* sens,
+                                     float sens_scale, float b, const jp_tof* t, void* stream) {
+  clear_error();
+  if (!pl) return fail(JP_ERR_ARG, "plan is NULL");
+  if (!(pl->opts.flags & JP_PLAN_INTERLEAVED)) return fail(JP_ERR_STATE, "OSEM subsets need a JP_PLAN_INTERLEAVED plan");
+  if (!pl->has_tof_bin) return fail(JP_ERR_STATE, "TOF listmode needs a plan created with tof_bin");
+  if (f0 < 0 || f1 > pl->n_frames || f0 > f1) return fail(JP_ERR_ARG, "frame range outside the plan");
+  if (!x || !sens) return fail(JP_ERR_ARG, "x / sens is NULL");
+  if (!aligned(x, 4) || !aligned(sens, 4)) return fail(JP_ERR_ALIGN, "arrays must be 4-byte aligned");
+  if (!(sens_scale > 0.f) || !isfinite(sens_scale)) return fail(JP_ERR_ARG, "sens_scale must be finite and > 0");
+  if (!(b >= 0.f) || !isfinite(b)) return fail(JP_ERR_ARG, "b must be finite and >= 0");
+  ProjParams p;
+  std::memset(&p, 0, sizeof(p));
+  int rc = make_geom(&pl->g, &p.g);
+  if (rc) return rc;
+  rc = make_tof(t, false, &p.tof);
+  if (rc) return rc;
+  const int64_t start = pl->frame_off_host[f0], end = pl->frame_off_host[f1];
+  p.lor = pl->lor + 2 * start;
+  p.perm = pl->perm + start;
+  p.frame_off = pl->frame_off_dev;
+  p.n_frames = pl->n_frames;
+  p.n = end - start;
+  p.ql = pl->ql;
+  p.axis_used = pl->axis_used;
+  p.shared = 1;
+  p.kfast = 1;
+  p.img_in = x;
+  p.quads = pl->quads;
+  p.quads_bp = pl->quads + pl->ql.slot;
+  p.bg = b;
+  p.sens = sens;
+  p.sens_scale = sens_scale;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t max_quad = std::max(std::max(p.ql.size[0], p.ql.size[1]), p.ql.size[2]);
+  dim3 qgrid(aux_grid(max_quad, 256), 3);
+  quad_build_kernel<<<qgrid, 256, 0, st>>>(p);
+  count_launch();
+  {
+    ProjParams z = p;
+    z.quads = p.quads_bp;
+    quad_zero_kernel<<<qgrid, 256, 0, st>>>(z);
+    count_launch();
+  }
+  JP_TRY_CUDA(cudaGetLastError());
+  if (p.n > 0) {
+    const bool lut = !(pl->opts.flags & JP_PLAN_TOF_EXACT);
+    int lpw = pl->opts.lors_per_warp;
+    if (lpw != 1 && lpw != 2) lpw = 4;
+    const int block = std::min(pl->opts.block, kMaxBlock);
+    const size_t smem = lut ? kLut * sizeof(float2) : 0;
+    auto pick = [&](auto kern) -> int {
+      int per_sm = 0;
+      JP_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem));
+      int64_t grid = (int64_t)sm_count() * (per_sm < 1 ? 1 : per_sm);
+      const int64_t need = (p.n + block - 1) / block;
+      if (grid > need) grid = need;
+      kern<<<(unsigned)(grid < 1 ? 1 : grid), block, smem, st>>>(p);
+      count_launch();
+      JP_TRY_CUDA(cudaGetLastError());
+      return JP_OK;
+    };
+    if (lut) rc = (lpw == 1) ? pick(osem_kernel<true, 32>) : (lpw == 2 ? pick(osem_kernel<true, 16>) : pick(osem_kernel<true, 8>));
+    else rc = (lpw == 1) ? pick(osem_kernel<false, 32>) : (lpw == 2 ? pick(osem_kernel<false, 16>) : pick(osem_kernel<false, 8>));
+    if (rc) return rc;
+  }
+  const int64_t nvox = (int64_t)p.g.n[0] * p.g.n[1] * p.g.n[2];
+  osem_update_kernel<<<aux_grid(nvox, 256), 256, 0, st>>>(p, x);
   count_launch();
   JP_TRY_CUDA(cudaGetLastError());
   return JP_OK;

@@ -25,6 +25,7 @@ F32 = ctypes.c_float
 TOF_MODES = {"nontof": 0, "tof_sino": 1, "tof_lm": 2}
 JP_PLAN_KEEP_ORDER = 1
 JP_PLAN_TOF_EXACT = 2
+JP_PLAN_INTERLEAVED = 4
 
 
 class JosephError(RuntimeError):
@@ -43,7 +44,7 @@ class TofC(ctypes.Structure):
 
 class PlanOptsC(ctypes.Structure):
     _fields_ = [("block", I32), ("slope_bins", I32), ("offset_bins", I32), ("window_bins", I32),
-                ("tof_bin_width", F32), ("flags", I32)]
+                ("tof_bin_width", F32), ("lors_per_warp", I32), ("flags", I32)]
 
 
 _lib = None
@@ -67,6 +68,8 @@ _SIGS = {
     "jp_osem_update": [P, P, P, F32, I64, I32, I64, I64, P],
     "jp_sum_f64": [P, I64, P, P],
     "jp_count_samples": [P, I32, P, P, P],
+    "jp_osem_subset_tof_lm": [P, I32, I32, P, P, F32, F32, P, P],
+    "jp_osem_init": [P, P, I64, P],
 }
 
 
@@ -179,10 +182,11 @@ class Plan:
 
 
 def _opts(block=0, slope_bins=0, offset_bins=0, window_bins=0, tof_bin_width=0.0, keep_order=False,
-          tof_exact=False):
-    flags = (JP_PLAN_KEEP_ORDER if keep_order else 0) | (JP_PLAN_TOF_EXACT if tof_exact else 0)
+          tof_exact=False, lors_per_warp=0, interleaved=False):
+    flags = ((JP_PLAN_KEEP_ORDER if keep_order else 0) | (JP_PLAN_TOF_EXACT if tof_exact else 0)
+             | (JP_PLAN_INTERLEAVED if interleaved else 0))
     return PlanOptsC(int(block), int(slope_bins), int(offset_bins), int(window_bins),
-                     float(tof_bin_width), flags)
+                     float(tof_bin_width), int(lors_per_warp), flags)
 
 
 def jp_plan_create_batch(xs, xe, geom, frame_offsets, tof_bin=None, delta=None, stream=None,
@@ -201,6 +205,17 @@ def jp_plan_create_batch(xs, xe, geom, frame_offsets, tof_bin=None, delta=None, 
 
 def jp_plan_create(xs, xe, geom, tof_bin=None, delta=None, stream=None, **opts) -> Plan:
     return jp_plan_create_batch(xs, xe, geom, [0, int(xs.shape[0])], tof_bin, delta, stream, **opts)
+
+
+def jp_plan_create_subsets(xs, xe, geom, n_subsets, tof_bin=None, delta=None, stream=None, **opts) -> Plan:
+    """Plan whose frames are the listmode OSEM subsets e mod n_subsets
+    (JP_PLAN_INTERLEAVED); all subsets share one image."""
+    n = int(xs.shape[0])
+    off = [0] * n_subsets + [n]
+    plan = jp_plan_create_batch(xs, xe, geom, off, tof_bin, delta, stream, interleaved=True, **opts)
+    plan.frame_offsets = [sum(n // n_subsets + (1 if f < n % n_subsets else 0) for f in range(m))
+                          for m in range(n_subsets + 1)]
+    return plan
 
 
 def jp_plan_rebind(plan: Plan, xs, xe, frame_offsets=None, tof_bin=None, delta=None, stream=None):
@@ -332,6 +347,24 @@ def jp_osem_update(x, bp, sens, scale, nvox, n_frames=1, img_stride=None, s_stri
     return x
 
 
+def jp_osem_subset_tof_lm(plan: Plan, f0: int, f1: int, x, sens, sens_scale: float, b: float, tof,
+                          stream=None):
+    """x <- x / (sens*sens_scale) * A_S^T (1/(A_S x + b)) for the events of
+    subset frames [f0, f1) of an interleaved plan (one fused pass per event)."""
+    t = tof_params(tof)
+    _check(load().jp_osem_subset_tof_lm(plan.handle, int(f0), int(f1), _ptr(x, torch.float32, "x"),
+                                        _ptr(sens, torch.float32, "sens"), float(sens_scale), float(b),
+                                        ctypes.byref(t), _stream(stream)))
+    return x
+
+
+def jp_osem_init(x, sens, stream=None):
+    """x = sens > 0 ? 1 : 0 (listmode OSEM start image)."""
+    _check(load().jp_osem_init(_ptr(x, torch.float32, "x"), _ptr(sens, torch.float32, "sens"), int(x.numel()),
+                               _stream(stream)))
+    return x
+
+
 def jp_sum_f64(x, out=None, stream=None):
     out = torch.empty((), dtype=torch.float64, device=x.device) if out is None else out
     _check(load().jp_sum_f64(_ptr(x, torch.float32, "x"), int(x.numel()), _ptr(out, torch.float64, "out"),
@@ -360,6 +393,8 @@ def jp_version() -> str:
 # short aliases
 plan_create = jp_plan_create
 plan_create_batch = jp_plan_create_batch
+plan_create_subsets = jp_plan_create_subsets
+osem_subset_tof_lm = jp_osem_subset_tof_lm
 plan_rebind = jp_plan_rebind
 fwd = jp_fwd
 back = jp_back

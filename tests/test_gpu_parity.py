@@ -45,13 +45,13 @@ def small():
     return g, img, xs, xe, y, p_or, b_or
 
 
-@pytest.mark.parametrize("planned", [True, False])
+@pytest.mark.parametrize("planned", [0, 1, 4, 32, False])
 def test_small_nontof(ops, small, planned):
     g, img, xs, xe, y, p_or, b_or = small
     dxs, dxe, dimg, dy = cuda(xs), cuda(xe), cuda(img), cuda(y)
     out = torch.zeros(g.shape, device="cuda")
-    if planned:
-        plan = ops.jp_plan_create(dxs, dxe, g)
+    if planned is not False:
+        plan = ops.jp_plan_create(dxs, dxe, g, lors_per_warp=planned)
         p = ops.jp_fwd(plan, dimg)
         ops.jp_back(plan, dy, out)
     else:
@@ -134,7 +134,7 @@ def lm_events(clinical_img):
     return xs.numpy(), xe.numpy(), tb.numpy()
 
 
-@pytest.mark.parametrize("planned", ["lut", "exact", "planless"])
+@pytest.mark.parametrize("planned", ["lut", "exact", "planless", "lpw1", "lpw2", "lpw32"])
 def test_tof_lm(ops, clinical_img, lm_events, planned):
     g = synth.GEOM_CLINICAL
     tof = synth.TOF_CLINICAL
@@ -146,8 +146,9 @@ def test_tof_lm(ops, clinical_img, lm_events, planned):
     out = torch.zeros(g.shape, device="cuda")
     dtb = cuda(tb, torch.int16)
     if planned != "planless":
+        lpw = int(planned[3:]) if planned.startswith("lpw") else 0
         plan = ops.jp_plan_create(cuda(xs), cuda(xe), g, tof_bin=dtb, tof_bin_width=tof.bin_width,
-                                  tof_exact=(planned == "exact"))
+                                  tof_exact=(planned == "exact"), lors_per_warp=lpw)
         p = ops.jp_fwd_tof_lm(plan, cuda(clinical_img), tof)
         ops.jp_back_tof_lm(plan, cuda(y), tof, out)
     else:
