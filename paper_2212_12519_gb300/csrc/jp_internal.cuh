@@ -300,4 +300,5 @@ struct jp_plan_s {
   float4* quads;          // [quad_slots * ql.slot]
   int32_t quad_slots;     // frames with their own image, or 2 (image + back projection) when interleaved
   int32_t* axis_used;     // [frame_capacity * 3]: frame f has LORs with principal axis a
+  uint32_t* work_counter; // chunk counter of the persistent projection kernels
 };

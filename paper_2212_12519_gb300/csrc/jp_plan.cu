@@ -304,6 +304,7 @@ void free_plan(jp_plan p) {
   cudaFreeHost(p->frame_off_host);
   cudaFree(p->quads);
   cudaFree(p->axis_used);
+  cudaFree(p->work_counter);
   delete p;
 }
 
@@ -387,6 +388,7 @@ extern "C" int jp_plan_create_batch(jp_plan* out, const float* xs, const float* 
   p->quad_slots = interleaved ? 2 : std::max<int32_t>(n_frames, 1);
   if (e == cudaSuccess) e = cudaMalloc(&p->quads, sizeof(float4) * (size_t)p->ql.slot * (size_t)p->quad_slots);
   if (e == cudaSuccess) e = cudaMalloc(&p->axis_used, sizeof(int32_t) * 3 * (size_t)n_frames);
+  if (e == cudaSuccess) e = cudaMalloc(&p->work_counter, 256);
   if (e != cudaSuccess) {
     cudaGetLastError();
     free_plan(p);

@@ -98,6 +98,10 @@ struct ProjParams {
   float bg;           // additive background b
   const float* sens;  // sensitivity image
   float sens_scale;
+  // persistent kernels take chunks of LORs from this counter (reset by the
+  // workspace kernel launched just before them), so the chunks in flight
+  // stay a contiguous window of the binned order (one frame's image at a time)
+  unsigned int* counter;
 };
 
 __device__ __forceinline__ int frame_of(const int64_t* __restrict__ off, int n_frames, int64_t i) {
@@ -162,8 +166,14 @@ __global__ void __launch_bounds__(kMaxBlock) planned_kernel(const ProjParams p) 
   }
   const float inv_h = (MODE != 0) ? (float)(kLut - 1) / (2.f * T.R) : 0.f;
   const int N = T.nbins;
-  const int64_t step = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += step) {
+  __shared__ unsigned int tile_s;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) tile_s = atomicAdd(p.counter, 1u);
+    __syncthreads();
+    const int64_t i = (int64_t)tile_s * blockDim.x + threadIdx.x;
+    if ((int64_t)tile_s * blockDim.x >= p.n) break;
+    if (i >= p.n) continue;
     const float4 A = __ldg(p.lor + 2 * i);
     const float4 B = __ldg(p.lor + 2 * i + 1);
     const float xs[3] = {A.x, A.y, A.z};
@@ -335,9 +345,11 @@ __global__ void __launch_bounds__(kMaxBlock) group_kernel(const ProjParams p) {
   const float inv_h = (MODE == 2) ? (float)(kLut - 1) / (2.f * T.R) : 0.f;
   const int lane = threadIdx.x & 31;
   const int grp = lane / G, gl = lane - grp * G;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t base = warp * 32; base < p.n; base += nwarps * 32) {
+  for (;;) {
+    unsigned int chunk = 0;
+    if (lane == 0) chunk = atomicAdd(p.counter, 1u);
+    const int64_t base = (int64_t)__shfl_sync(0xffffffffu, chunk, 0) * 32;
+    if (base >= p.n) break;
     // ---- per-lane setup of LOR base + lane ----
     const int64_t i = base + lane;
     Ray r;
@@ -455,9 +467,11 @@ __global__ void __launch_bounds__(kMaxBlock) osem_kernel(const ProjParams p) {
   const float inv_h = (float)(kLut - 1) / (2.f * T.R);
   const int lane = threadIdx.x & 31;
   const int grp = lane / G, gl = lane - grp * G;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t base = warp * 32; base < p.n; base += nwarps * 32) {
+  for (;;) {
+    unsigned int chunk = 0;
+    if (lane == 0) chunk = atomicAdd(p.counter, 1u);
+    const int64_t base = (int64_t)__shfl_sync(0xffffffffu, chunk, 0) * 32;
+    if (base >= p.n) break;
     const int64_t i = base + lane;
     Ray r;
     r.k0 = 1; r.k1 = 0;
@@ -568,6 +582,7 @@ __global__ void osem_update_kernel(const ProjParams p, float* __restrict__ x) {
 // ---------------------------------------------------------------------------
 
 __global__ void quad_build_kernel(const ProjParams p) {
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && p.counter) *p.counter = 0u;
   const int slot = blockIdx.y / 3, a = blockIdx.y - 3 * (blockIdx.y / 3);
   if (!slot_axis_used(p.axis_used, slot, a, p.shared, p.n_frames)) return;
   const int b = (a == 0) ? 1 : 0, c = (a == 2) ? 1 : 2;
@@ -608,6 +623,7 @@ __global__ void quad_build_kernel(const ProjParams p) {
 }
 
 __global__ void quad_zero_kernel(const ProjParams p) {
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && p.counter) *p.counter = 0u;
   const int slot = blockIdx.y / 3, a = blockIdx.y - 3 * (blockIdx.y / 3);
   if (!slot_axis_used(p.axis_used, slot, a, p.shared, p.n_frames)) return;
   const int64_t total = sel3(a, p.ql.size[0], p.ql.size[1], p.ql.size[2]);
@@ -890,6 +906,7 @@ int planned(jp_plan pl, int mode, bool back, const float* in, float* out, int64_
   p.ql = pl->ql;
   p.axis_used = pl->axis_used;
   p.shared = (img_stride == 0 || pl->n_frames == 1) ? 1 : 0;
+  p.counter = pl->work_counter;
   if (back) { p.proj_in = in; p.img_out = out; } else { p.img_in = in; p.proj_out = out; }
   const int slots = p.shared ? 1 : pl->n_frames;
   if (slots * 3 > 65535) return fail(JP_ERR_ARG, "too many frames with distinct images (max 21845)");
@@ -1061,6 +1078,7 @@ extern "C" int jp_osem_subset_tof_lm(jp_plan pl, int32_t f0, int32_t f1, float* 
   p.bg = b;
   p.sens = sens;
   p.sens_scale = sens_scale;
+  p.counter = pl->work_counter;
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t max_quad = std::max(std::max(p.ql.size[0], p.ql.size[1]), p.ql.size[2]);
   dim3 qgrid(aux_grid(max_quad, 256), 3);

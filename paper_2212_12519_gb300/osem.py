@@ -98,10 +98,17 @@ class LMOSEMFrame:
         return self.x
 
     def capture(self):
-        """Captures one iteration (n_sub updates) into a CUDA graph."""
+        """Captures one iteration (n_sub updates) into a CUDA graph (on a
+        side stream when the frame runs on the default stream)."""
         self.graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(self.graph, stream=self.stream):
+        cap = self.stream
+        if cap == torch.cuda.default_stream(cap.device):
+            cap = torch.cuda.Stream(device=cap.device)
+            cap.wait_stream(self.stream)
+        with torch.cuda.graph(self.graph, stream=cap):
             self._updates(1)
+        if cap is not self.stream:
+            self.stream.wait_stream(cap)
         return self.graph
 
     def run_graph(self):
