@@ -244,6 +244,30 @@ int jp_count_samples(jp_plan p, int32_t tof_mode, const jp_tof* t, uint64_t* out
 /* total number of kernels this library has launched in the process */
 uint64_t jp_launch_count(void);
 
+/*
+ * jp_back_tof_lm_noalloc -- TOF listmode back projection that allocates
+ * nothing, for callers that cannot allocate device memory: code running
+ * while a CUDA graph is being captured, where an allocation is not allowed;
+ * engines whose device memory is fully handed out by their own pool or a
+ * fixed real-time budget; and callbacks where cudaMalloc would stall the
+ * whole device.  The paper has no counterpart; it is a service variant of
+ * jp_back_lors (tof_mode 2) with the same arguments and result
+ * (img_accum += A^T proj, caller order, same tolerance as the other back
+ * projections).
+ * Its scratch is a workspace compiled into the library: 2^20 entries of 16
+ * bytes (16 MiB), held by every GPU that loads the library until the process
+ * exits.  The image must fit it: sum over a of n_a (n_b + 2)(n_c + 2) <= 2^20
+ * (for instance 64 x 64 x 16, or about 70^3), else JP_ERR_ARG.  The first
+ * call on a device looks the workspace address up (cudaGetSymbolAddress),
+ * so make that first call before any stream capture.  Every call shares the
+ * one workspace (it is cleared at the start of each call): calls that
+ * overlap on the GPU, on any stream, race and give wrong results.
+ * Errors: JP_ERR_ARG, JP_ERR_ALIGN, JP_ERR_CUDA.
+ */
+int jp_back_tof_lm_noalloc(const float* xstart, const float* xend, const int16_t* tof_bin,
+                           const float* tof_center_offset, int64_t n_lor, const jp_image_geom* g,
+                           const jp_tof* t, const float* proj, float* img_accum, void* stream);
+
 /* thread-local message of the last failing call ("" if none) */
 const char* jp_last_error(void);
 

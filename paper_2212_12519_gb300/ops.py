@@ -70,6 +70,7 @@ _SIGS = {
     "jp_count_samples": [P, I32, P, P, P],
     "jp_osem_subset_tof_lm": [P, I32, I32, P, P, F32, F32, P, P],
     "jp_osem_init": [P, P, I64, P],
+    "jp_back_tof_lm_noalloc": [P, P, P, P, I64, P, P, P, P, P],
 }
 
 
@@ -325,6 +326,20 @@ def jp_back_lors(xs, xe, proj, geom, img_accum, tof_mode="nontof", tof=None, tof
                                int(xs.shape[0]), ctypes.byref(g), m, ctypes.byref(t) if t is not None else None,
                                _ptr(proj, torch.float32, "proj"), _ptr(img_accum, torch.float32, "img_accum"),
                                _stream(stream)))
+    return img_accum
+
+
+def jp_back_tof_lm_noalloc(xs, xe, proj, geom, img_accum, tof, tof_bin, delta=None, stream=None):
+    """img_accum += A^T proj (TOF listmode) without any device allocation:
+    the workspace is fixed inside the library (images up to
+    sum_a n_a (n_b+2)(n_c+2) <= 2^20).  Overlapping calls race."""
+    pxs, pxe = _lors(xs, xe)
+    g = image_geom(geom)
+    t = tof_params(tof)
+    _check(load().jp_back_tof_lm_noalloc(pxs, pxe, _ptr(tof_bin, torch.int16, "tof_bin"),
+                                         _ptr(delta, torch.float32, "delta"), int(xs.shape[0]), ctypes.byref(g),
+                                         ctypes.byref(t), _ptr(proj, torch.float32, "proj"),
+                                         _ptr(img_accum, torch.float32, "img_accum"), _stream(stream)))
     return img_accum
 
 
