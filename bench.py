@@ -158,8 +158,12 @@ def run_ours(args):
     W = make_tof_lm_batch(rank, n_frames, epf, dev)
     g, tof = W["geom"], W["tof"]
     n_total = W["xs"].shape[0]
+    opts = {}
+    if not args.no_autotune:
+        from paper_2212_12519_gb300 import autotune
+        opts = autotune.tune(W["xs"][:epf], W["xe"][:epf], g, mode="tof_lm", tof=tof, tof_bin=W["tb"][:epf])
     plan = ops.jp_plan_create_batch(W["xs"], W["xe"], g, W["offsets"], tof_bin=W["tb"],
-                                    tof_bin_width=tof.bin_width)
+                                    tof_bin_width=tof.bin_width, **opts)
     x = W["x"].clone().requires_grad_(True)
     stream = torch.cuda.current_stream()
 
@@ -210,11 +214,13 @@ def run_ours(args):
     launches0 = ops.jp_launch_count()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
     t0.record(stream)
     for _ in range(args.steps):
         loss = step()
     t1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     launches = ops.jp_launch_count() - launches0
     if ws > 1:
         dist.barrier()
@@ -234,6 +240,11 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, W, plan, g, tof, dev, ws)
+    # scattered-reduction ceiling (one 16-byte RED per plane sample bounds the back projection)
+    red = ops.jp_bench_red()
+    cpu_sample = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu_sample = _oracle_events(W, min(W["xs"].shape[0], 8_000_000))
     plan.destroy()
     del W["xs"], W["xe"], W["tb"], W["w"], W["bvec"]
     torch.cuda.empty_cache()
@@ -249,6 +260,8 @@ def run_ours(args):
         nvox = int(np.prod(g.shape))
         alg_bytes = n_total * (24 + 2 + 4) + n_frames * nvox * 4 * (2 if dom == "back" else 1)
         achieved = alg_bytes / (kern[dom] / 1e3) / 1e9
+        # binding resource: one 16-byte reduction per sample (back) vs the measured ceiling
+        red_rate = samples / (kern["back"] / 1e3)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -256,7 +269,7 @@ def run_ours(args):
             "config": {"workload": f"tof_lm_batch{n_frames}x{epf // 1_000_000}M_200x200x71",
                        "frames_per_gpu": n_frames, "events_per_frame": epf, "image": list(g.shape),
                        "tof_bins": tof.n_bins, "l2": "inputs (>10 GB/step) larger than L2, no flush",
-                       "parallelism": f"dp{ws} (independent batches)"},
+                       "parallelism": f"dp{ws} (independent batches)", "plan_opts": opts},
             "kernel_ms": kern,
             "samples_per_step": samples,
             "events_per_s_excl_binning": n_total * ws / ((ms - kern.get("bin", 0.0)) / 1e3),
@@ -264,13 +277,17 @@ def run_ours(args):
                          "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
                          "traffic": None, "peak_source": peak_kind,
                          "alg_bytes_per_launch": alg_bytes},
+            "binding_roofline": {"kernel": "back_tof_lm", "resource": "scattered 16-byte L2 reductions",
+                                 "achieved": red_rate, "peak": red["reductions_per_s"], "unit": "reductions/s",
+                                 "frac": red_rate / red["reductions_per_s"],
+                                 "peak_source": "jp_bench_red (measured in this run)"},
             "clocks": clk,
             "gpu_launches": int(launches),
             "e2e": e2e,
             "serving": serving,
         }
-        if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(W, g, tof, target_s=args.cpu_seconds)
+        if cpu_sample is not None:
+            line["cpu_baseline"] = cpu_baseline(cpu_sample, W["bvals"][0], g, tof, n_total, target_s=args.cpu_seconds)
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
@@ -316,6 +333,123 @@ def run_e2e(args, W, plan, g, tof, dev, ws):
     ms = t0.elapsed_time(t1) / n
     return {"value": W["xs"].shape[0] * ws / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
             "steps": n, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+
+# ---------------------------------------------------------------------------
+# sinogram workloads: small non-TOF, clinical non-TOF, TOF sinogram
+# ---------------------------------------------------------------------------
+SINO_WORKLOADS = {
+    # name: (sino spec, image geom, phantom, seed base, tof?)
+    "sino_small": ("SINO_SMALL", "GEOM_SMALL", "PHANTOM_SMALL", 1000, False),
+    "sino_clinical": ("SINO_CLINICAL", "GEOM_CLINICAL", "PHANTOM_CLINICAL", 2000, False),
+    "tof_sino": ("SINO_TOF", "GEOM_CLINICAL", "PHANTOM_CLINICAL", 3000, True),
+}
+
+
+def run_sino(args):
+    """One step = forward + back projection of every LOR of the sinogram
+    (LOR endpoints and their plan are computed once, outside the timed
+    region, as the paper excludes LOR set-up).  value = LORs projected
+    forward and back per second."""
+    from paper_2212_12519_gb300 import build as jbuild, ops, synth
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    jbuild.build()
+    ops.load()
+    spec_n, geom_n, ph_n, sb, is_tof = SINO_WORKLOADS[args.workload]
+    spec, g, phs = getattr(synth, spec_n), getattr(synth, geom_n), getattr(synth, ph_n)
+    tof = synth.TOF_CLINICAL if is_tof else None
+    img = synth.ellipsoid_phantom(g, phs, sb + 1, device=dev)
+    xs, xe = synth.sinogram_lors(spec, device=dev)
+    n = xs.shape[0]
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(sb + 2)
+    if is_tof:
+        y = torch.poisson(torch.full((n, tof.n_bins), 2.0, device=dev), generator=gen)
+    else:
+        y = torch.rand(n, generator=gen, device=dev)
+    plan = ops.jp_plan_create(xs, xe, g)
+    out = torch.zeros(g.shape, device=dev)
+    stream = torch.cuda.current_stream()
+    tim = {"fwd": [], "back": []}
+
+    def rec(name, fn):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        tim[name].append((a, b))
+
+    def step(record=True):
+        f = (lambda: ops.jp_fwd_tof_sino(plan, img, tof)) if is_tof else (lambda: ops.jp_fwd(plan, img))
+        bk = (lambda: ops.jp_back_tof_sino(plan, y, tof, out)) if is_tof else (lambda: ops.jp_back(plan, y, out))
+        if record:
+            rec("fwd", f)
+            rec("back", bk)
+        else:
+            f()
+            bk()
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = ops.jp_launch_count()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
+    t0.record(stream)
+    for _ in range(args.steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    launches = ops.jp_launch_count() - launches0
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1) / args.steps
+    kern = {k: statistics.mean(a.elapsed_time(b) for a, b in v) for k, v in tim.items()}
+    samples = ops.jp_count_samples(plan, "nontof")
+    red = ops.jp_bench_red()
+    peaks, peak_kind = measured_peaks()
+    nb = tof.n_bins if is_tof else 1
+    dom = "back" if kern["back"] >= kern["fwd"] else "fwd"
+    nvox = int(np.prod(g.shape))
+    alg = n * (24 + 4 * nb) + nvox * 4 * (2 if dom == "back" else 1)
+    achieved = alg / (kern[dom] / 1e3) / 1e9
+    line = {"metric": "LOR projections (fwd+back)/s", "value": n / (ms / 1e3), "unit": "LOR/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "lors": n, "image": list(g.shape), "tof_bins": nb,
+                       "l2": "LOR arrays larger than L2" if n * 24 > 200e6 else "small case, L2-resident"},
+            "kernel_ms": kern, "samples_per_step": samples,
+            "roofline": {"bound": "hbm", "kernel": f"{dom}_{args.workload}", "achieved": achieved,
+                         "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                         "traffic": None, "peak_source": peak_kind, "alg_bytes_per_launch": alg},
+            "binding_roofline": {"kernel": f"back_{args.workload}", "resource": "scattered 16-byte L2 reductions",
+                                 "achieved": samples / (kern["back"] / 1e3), "peak": red["reductions_per_s"],
+                                 "unit": "reductions/s", "frac": samples / (kern["back"] / 1e3) / red["reductions_per_s"]},
+            "clocks": clk, "gpu_launches": int(launches)}
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        threads = os.cpu_count() or 1
+        m = min(n, args.cpu_lors)
+        sx, se = xs[:m].cpu().numpy(), xe[:m].cpu().numpy()
+        yy = y[:m].cpu().numpy()
+        im = img.cpu().numpy()
+        mode = "tof_sino" if is_tof else "nontof"
+        t = time.perf_counter()
+        oracle.fwd(sx, se, im, g, mode, tof, threads=threads)
+        oracle.back(sx, se, yy, g, mode, tof, threads=threads)
+        dt = time.perf_counter() - t
+        line["cpu_baseline"] = {"value": m / dt, "unit": "LOR/s", "cores": threads, "kind": "oracle",
+                                "sample": f"first {m} of {n} LORs, FP64 fwd+back, {dt:.1f} s"}
+    print(json.dumps(line), flush=True)
+    plan.destroy()
 
 
 # ---------------------------------------------------------------------------
@@ -376,22 +510,23 @@ def oracle_step(xs, xe, tb, img, w, g, tof, b, threads):
     oracle.back(xs, xe, q, g, "tof_lm", tof, tof_bin=tb, threads=threads)
 
 
-def cpu_baseline(W, g, tof, target_s=12.0):
+def cpu_baseline(sample, b, g, tof, n_total, target_s=12.0):
+    """The FP64 oracle (fwd + back, all host cores) on the first events of
+    frame 0, sized to take about ``target_s`` seconds."""
     import oracle
     oracle.build()
     threads = os.cpu_count() or 1
-    n0 = 100_000
-    xs, xe, tb, img, w = _oracle_events(W, n0)
+    xs, xe, tb, img, w = sample
+    n0 = min(100_000, len(xs))
     t = time.perf_counter()
-    oracle_step(xs, xe, tb, img, w, g, tof, W["bvals"][0], threads)
+    oracle_step(xs[:n0], xe[:n0], tb[:n0], img, w[:n0], g, tof, b, threads)
     dt = time.perf_counter() - t
-    n = int(min(W["xs"].shape[0], max(n0, n0 * target_s / max(dt, 1e-3))))
-    xs, xe, tb, img, w = _oracle_events(W, n)
+    n = int(min(len(xs), max(n0, n0 * target_s / max(dt, 1e-3))))
     t = time.perf_counter()
-    oracle_step(xs, xe, tb, img, w, g, tof, W["bvals"][0], threads)
+    oracle_step(xs[:n], xe[:n], tb[:n], img, w[:n], g, tof, b, threads)
     dt = time.perf_counter() - t
     return {"value": n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"first {n} events of frame 0 (of {W['xs'].shape[0]}), FP64 fwd+back, {dt:.1f} s"}
+            "sample": f"first {n} events of frame 0 (of {n_total} in the batch), FP64 fwd+back, {dt:.1f} s"}
 
 
 def run_reference(args):
@@ -446,9 +581,26 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=200)
     ap.add_argument("--serving-rates", default="1.0")
+    ap.add_argument("--workload", default="tof_lm",
+                    choices=["tof_lm", "sino_small", "sino_clinical", "tof_sino", "osem"])
+    ap.add_argument("--cpu-lors", type=int, default=200_000)
+    ap.add_argument("--budget-gb", type=float, default=None)
+    ap.add_argument("--no-graphs", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload in SINO_WORKLOADS:
+        run_sino(args)
+    elif args.workload == "osem":
+        from paper_2212_12519_gb300 import build as jbuild, ops
+        jbuild.build()
+        ops.load()
+        rates = [float(r) for r in args.serving_rates.split(",")]
+        out = run_serving(n_requests=args.serving_requests, rates=rates,
+                          budget_gb=args.budget_gb, use_graphs=not args.no_graphs)
+        print(json.dumps({"metric": "served listmode OSEM frames/s; p50/p99 latency", "workload": "osem_stream",
+                          **out}), flush=True)
     else:
         run_ours(args)
 

@@ -268,6 +268,18 @@ int jp_back_tof_lm_noalloc(const float* xstart, const float* xend, const int16_t
                            const float* tof_center_offset, int64_t n_lor, const jp_image_geom* g,
                            const jp_tof* t, const float* proj, float* img_accum, void* stream);
 
+/*
+ * jp_bench_red -- measurement helper (not part of the projector): times
+ * `iters` launches of a kernel in which every thread issues `per_thread`
+ * 16-byte vector reductions (red.add of a float4) at pseudo-random 16-byte
+ * aligned positions of the device buffer `buf` (n_entries float4, caller
+ * allocated; its contents are changed).  *ms_out receives the mean time of
+ * one launch; the rate is (blocks*threads*per_thread) / time.  It gives the
+ * device's scattered-reduction ceiling that bounds the back projections.
+ */
+int jp_bench_red(float* buf, int64_t n_entries, int32_t per_thread, int32_t iters, float* ms_out,
+                 void* stream);
+
 /* thread-local message of the last failing call ("" if none) */
 const char* jp_last_error(void);
 

@@ -63,6 +63,19 @@ __global__ void sum_f64_kernel(const float* __restrict__ x, int64_t n, double* o
   }
 }
 
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+  x ^= x >> 16; x *= 0x7feb352dU; x ^= x >> 15; x *= 0x846ca68bU; x ^= x >> 16;
+  return x;
+}
+
+__global__ void bench_red_kernel(float4* buf, uint32_t n, int per_thread) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int r = 0; r < per_thread; ++r) {
+    const uint32_t i = mix32(t * 131u + (uint32_t)r) % n;
+    atomicAdd(buf + i, make_float4(1.f, 1.f, 1.f, 1.f));
+  }
+}
+
 int grid_for(int64_t n, int block) {
   int64_t g = (n + block - 1) / block;
   int64_t cap = (int64_t)sm_count() * 8;
@@ -120,6 +133,35 @@ extern "C" int jp_osem_init(float* x, const float* s, int64_t n, void* stream) {
   if (n == 0) return JP_OK;
   init_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(x, s, n);
   count_launch();
+  JP_TRY_CUDA(cudaGetLastError());
+  return JP_OK;
+}
+
+extern "C" int jp_bench_red(float* buf, int64_t n_entries, int32_t per_thread, int32_t iters, float* ms_out,
+                            void* stream) {
+  clear_error();
+  if (!buf || !ms_out || n_entries < 1 || n_entries > (int64_t)UINT32_MAX || per_thread < 1 || iters < 1)
+    return fail(JP_ERR_ARG, "bad arguments");
+  if (!aligned(buf, 16)) return fail(JP_ERR_ALIGN, "buf must be 16-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int blocks = sm_count() * 32, threads = 256;
+  bench_red_kernel<<<blocks, threads, 0, st>>>(reinterpret_cast<float4*>(buf), (uint32_t)n_entries, per_thread);
+  count_launch();
+  cudaEvent_t a, b;
+  JP_TRY_CUDA(cudaEventCreate(&a));
+  JP_TRY_CUDA(cudaEventCreate(&b));
+  JP_TRY_CUDA(cudaEventRecord(a, st));
+  for (int i = 0; i < iters; ++i) {
+    bench_red_kernel<<<blocks, threads, 0, st>>>(reinterpret_cast<float4*>(buf), (uint32_t)n_entries, per_thread);
+    count_launch();
+  }
+  JP_TRY_CUDA(cudaEventRecord(b, st));
+  JP_TRY_CUDA(cudaEventSynchronize(b));
+  float ms = 0.f;
+  JP_TRY_CUDA(cudaEventElapsedTime(&ms, a, b));
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  *ms_out = ms / iters;
   JP_TRY_CUDA(cudaGetLastError());
   return JP_OK;
 }

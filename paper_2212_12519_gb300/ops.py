@@ -71,6 +71,7 @@ _SIGS = {
     "jp_osem_subset_tof_lm": [P, I32, I32, P, P, F32, F32, P, P],
     "jp_osem_init": [P, P, I64, P],
     "jp_back_tof_lm_noalloc": [P, P, P, P, I64, P, P, P, P, P],
+    "jp_bench_red": [P, I64, I32, I32, P, P],
 }
 
 
@@ -394,6 +395,19 @@ def jp_count_samples(plan: Plan, tof_mode="nontof", tof=None, stream=None) -> in
     _check(load().jp_count_samples(plan.handle, TOF_MODES[tof_mode], ctypes.byref(t) if t is not None else None,
                                    _ptr(out, None, "out"), _stream(stream)))
     return int(out.item())
+
+
+def jp_bench_red(n_entries: int = 3_000_000, per_thread: int = 64, iters: int = 5, stream=None) -> dict:
+    """Scattered 16-byte reduction ceiling of the device (measurement helper):
+    reductions per second over an L2-resident buffer of n_entries float4."""
+    buf = torch.zeros((n_entries, 4), dtype=torch.float32, device="cuda")
+    ms = ctypes.c_float()
+    _check(load().jp_bench_red(_ptr(buf, torch.float32, "buf"), int(n_entries), int(per_thread), int(iters),
+                               ctypes.byref(ms), _stream(stream)))
+    import math
+    blocks = torch.cuda.get_device_properties(buf.device).multi_processor_count * 32
+    ops_ = blocks * 256 * per_thread
+    return {"reductions_per_s": ops_ / (ms.value / 1e3), "ms": ms.value, "buffer_bytes": n_entries * 16}
 
 
 def jp_launch_count() -> int:
