@@ -214,13 +214,13 @@ def run_ours(args):
     launches0 = ops.jp_launch_count()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.nvtx.range_push("timed")
+    rng_id = torch.cuda.nvtx.range_start("timed")  # process-wide: covers the autograd thread too
     t0.record(stream)
     for _ in range(args.steps):
         loss = step()
     t1.record(stream)
     torch.cuda.synchronize()
-    torch.cuda.nvtx.range_pop()
+    torch.cuda.nvtx.range_end(rng_id)
     launches = ops.jp_launch_count() - launches0
     if ws > 1:
         dist.barrier()
@@ -400,13 +400,13 @@ def run_sino(args):
     launches0 = ops.jp_launch_count()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.nvtx.range_push("timed")
+    rng_id = torch.cuda.nvtx.range_start("timed")
     t0.record(stream)
     for _ in range(args.steps):
         step()
     t1.record(stream)
     torch.cuda.synchronize()
-    torch.cuda.nvtx.range_pop()
+    torch.cuda.nvtx.range_end(rng_id)
     launches = ops.jp_launch_count() - launches0
     clk = clocks.stop()
     ms = t0.elapsed_time(t1) / args.steps
@@ -449,6 +449,32 @@ def run_sino(args):
         line["cpu_baseline"] = {"value": m / dt, "unit": "LOR/s", "cores": threads, "kind": "oracle",
                                 "sample": f"first {m} of {n} LORs, FP64 fwd+back, {dt:.1f} s"}
     print(json.dumps(line), flush=True)
+    plan.destroy()
+
+
+# ---------------------------------------------------------------------------
+# small case for ncu captures: one frame of --events TOF listmode events
+# (launch order: plan [key, scan x3, scatter, flags], then twice
+# [quad build, forward, quad zero, back, fold-back], then a rebind)
+# ---------------------------------------------------------------------------
+def run_profile_case(args):
+    from paper_2212_12519_gb300 import build as jbuild, ops, synth
+    jbuild.build()
+    ops.load()
+    dev = torch.device("cuda")
+    g, tof = synth.GEOM_CLINICAL, synth.TOF_CLINICAL
+    ph = synth.ellipsoid_phantom(g, synth.PHANTOM_CLINICAL, 4001, device=dev)
+    xs, xe, tb = synth.lm_events(ph, g, synth.SCANNER_CLINICAL, tof, args.events, seed=4051, device=dev)
+    y = torch.rand(args.events, device=dev)
+    img = torch.zeros(g.shape, device=dev)
+    plan = ops.jp_plan_create(xs, xe, g, tof_bin=tb, tof_bin_width=tof.bin_width)
+    for _ in range(2):
+        ops.jp_fwd_tof_lm(plan, ph, tof)
+        ops.jp_back_tof_lm(plan, y, tof, img)
+    ops.jp_plan_rebind(plan, xs, xe, tof_bin=tb)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": "tof_lm", "events": args.events,
+                      "samples": ops.jp_count_samples(plan, "tof_lm", tof)}))
     plan.destroy()
 
 
@@ -582,7 +608,7 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=200)
     ap.add_argument("--serving-rates", default="1.0")
     ap.add_argument("--workload", default="tof_lm",
-                    choices=["tof_lm", "sino_small", "sino_clinical", "tof_sino", "osem"])
+                    choices=["tof_lm", "sino_small", "sino_clinical", "tof_sino", "osem", "profile_case"])
     ap.add_argument("--cpu-lors", type=int, default=200_000)
     ap.add_argument("--budget-gb", type=float, default=None)
     ap.add_argument("--no-graphs", action="store_true")
@@ -590,6 +616,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "profile_case":
+        run_profile_case(args)
     elif args.workload in SINO_WORKLOADS:
         run_sino(args)
     elif args.workload == "osem":

@@ -270,7 +270,7 @@ inline QuadLayout quad_layout(const jp_image_geom& g) {
 }
 
 struct PlanDims {
-  int slope_bins, offset_bins, window_bins;
+  int slope_bins, offset_bins, window_bins, zoff_bins;
   int keys_per_frame;
   int keys_per_axis;
 };

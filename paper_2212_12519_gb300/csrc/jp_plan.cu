@@ -45,7 +45,7 @@ struct KeyParams {
   const int64_t* frame_off;
   int n_frames;
   DevGeom g;
-  int slope_bins, offset_bins, window_bins, keys_per_frame;
+  int slope_bins, offset_bins, window_bins, zoff_bins, keys_per_frame;
   float tof_width;  // > 0: listmode window binning
   int keep_order;
   int interleaved;  // frame of LOR j is j mod n_frames
@@ -89,7 +89,17 @@ __global__ void key_kernel(KeyParams p, uint32_t* __restrict__ keys, uint32_t* _
       const float cell_a = (float)(na + 2) / (float)p.window_bins;
       qw = clampi((int)floorf((ka + 1.f) / cell_a), 0, p.window_bins - 1);
     }
-    key = (uint32_t)(((a * p.slope_bins + qs) * p.offset_bins + qu) * p.window_bins + qw);
+    int qz = 0;
+    if (p.zoff_bins > 1) {
+      const int c = (a == 2) ? 1 : 2;
+      const int nc = sel3(c, g.n[0], g.n[1], g.n[2]);
+      const float oc = sel3(c, g.o[0], g.o[1], g.o[2]), ivc = sel3(c, g.inv_v[0], g.inv_v[1], g.inv_v[2]);
+      const float mc = 0.5f * (sel3(c, xs[0], xs[1], xs[2]) + sel3(c, xe[0], xe[1], xe[2]));
+      const float w = (fmaf(t, sel3(c, d0, d1, d2), mc) - oc) * ivc;
+      const float cell_w = (float)(nc + 2) / (float)p.zoff_bins;
+      qz = clampi((int)floorf((w + 1.f) / cell_w), 0, p.zoff_bins - 1);
+    }
+    key = (uint32_t)((((a * p.slope_bins + qs) * p.offset_bins + qu) * p.window_bins + qw) * p.zoff_bins + qz);
   }
   key += (uint32_t)f * (uint32_t)p.keys_per_frame;
   keys[j] = key;
@@ -180,16 +190,31 @@ __global__ void scan_apply_kernel(uint32_t* __restrict__ data, int64_t n, const 
   }
 }
 
+// Each thread places kScatterPer LORs; their slot claims are independent
+// returning atomics, so several are in flight at once (the claims, not the
+// bandwidth, bound this kernel).
+constexpr int kScatterPer = 4;
+
 __global__ void scatter_kernel(KeyParams p, const uint32_t* __restrict__ keys, uint32_t* __restrict__ cursor,
                                float4* __restrict__ lor, int32_t* __restrict__ perm) {
-  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= p.n) return;
-  uint32_t pos = p.keep_order ? (uint32_t)j : atomicAdd(cursor + keys[j], 1u);
-  float dl = p.delta ? p.delta[j] : 0.f;
-  int tb = p.tof_bin ? (int)p.tof_bin[j] : 0;
-  lor[2 * (int64_t)pos] = make_float4(p.xs[3 * j], p.xs[3 * j + 1], p.xs[3 * j + 2], dl);
-  lor[2 * (int64_t)pos + 1] = make_float4(p.xe[3 * j], p.xe[3 * j + 1], p.xe[3 * j + 2], __int_as_float(tb));
-  perm[pos] = (int32_t)j;
+  const int64_t base = ((int64_t)blockIdx.x * blockDim.x) * kScatterPer + threadIdx.x;
+  uint32_t pos[kScatterPer];
+#pragma unroll
+  for (int q = 0; q < kScatterPer; ++q) {
+    const int64_t j = base + (int64_t)q * blockDim.x;
+    pos[q] = 0;
+    if (j < p.n) pos[q] = p.keep_order ? (uint32_t)j : atomicAdd(cursor + keys[j], 1u);
+  }
+#pragma unroll
+  for (int q = 0; q < kScatterPer; ++q) {
+    const int64_t j = base + (int64_t)q * blockDim.x;
+    if (j >= p.n) continue;
+    const float dl = p.delta ? p.delta[j] : 0.f;
+    const int tb = p.tof_bin ? (int)p.tof_bin[j] : 0;
+    lor[2 * (int64_t)pos[q]] = make_float4(p.xs[3 * j], p.xs[3 * j + 1], p.xs[3 * j + 2], dl);
+    lor[2 * (int64_t)pos[q] + 1] = make_float4(p.xe[3 * j], p.xe[3 * j + 1], p.xe[3 * j + 2], __int_as_float(tb));
+    perm[pos[q]] = (int32_t)j;
+  }
 }
 
 // Frame f has LORs with principal axis a iff its keys of axis a hold any LOR.
@@ -260,7 +285,8 @@ int bind(jp_plan p, const float* xs, const float* xe, const int16_t* tof_bin, co
   kp.xs = xs; kp.xe = xe; kp.tof_bin = tof_bin; kp.delta = delta; kp.n = n;
   kp.frame_off = p->frame_off_dev; kp.n_frames = n_frames; kp.g = g;
   kp.slope_bins = p->dims.slope_bins; kp.offset_bins = p->dims.offset_bins;
-  kp.window_bins = p->dims.window_bins; kp.keys_per_frame = p->dims.keys_per_frame;
+  kp.window_bins = p->dims.window_bins; kp.zoff_bins = p->dims.zoff_bins;
+  kp.keys_per_frame = p->dims.keys_per_frame;
   kp.tof_width = p->opts.tof_bin_width;
   kp.keep_order = (p->opts.flags & JP_PLAN_KEEP_ORDER) ? 1 : 0;
   kp.interleaved = interleaved ? 1 : 0;
@@ -283,7 +309,8 @@ int bind(jp_plan p, const float* xs, const float* xe, const int16_t* tof_bin, co
     count_launch();
     JP_TRY_CUDA(cudaGetLastError());
   }
-  scatter_kernel<<<blocks, 256, 0, st>>>(kp, p->keys, p->hist, p->lor, p->perm);
+  scatter_kernel<<<(unsigned)((n + 256 * kScatterPer - 1) / (256 * kScatterPer)), 256, 0, st>>>(
+      kp, p->keys, p->hist, p->lor, p->perm);
   count_launch();
   axis_flags_kernel<<<(n_frames * 3 + 127) / 128, 128, 0, st>>>(p->hist, n_frames, p->dims.keys_per_frame,
                                                                p->dims.keys_per_axis, kp.keep_order,
@@ -343,13 +370,15 @@ extern "C" int jp_plan_create_batch(jp_plan* out, const float* xs, const float* 
   if (o.slope_bins == 0) o.slope_bins = 128;
   if (o.offset_bins == 0) o.offset_bins = 256;
   if (o.window_bins == 0) o.window_bins = 64;
-  if (o.slope_bins < 1 || o.offset_bins < 1 || o.window_bins < 1) return fail(JP_ERR_ARG, "bin counts must be >= 1");
+  if (o.zoff_bins == 0) o.zoff_bins = 1;
+  if (o.slope_bins < 1 || o.offset_bins < 1 || o.window_bins < 1 || o.zoff_bins < 1)
+    return fail(JP_ERR_ARG, "bin counts must be >= 1");
   if (o.lors_per_warp != 0 && o.lors_per_warp != 1 && o.lors_per_warp != 2 && o.lors_per_warp != 4 &&
       o.lors_per_warp != 32)
     return fail(JP_ERR_ARG, "opts.lors_per_warp must be 0, 1, 2, 4 or 32");
   if (!(o.tof_bin_width >= 0.f) || !isfinite(o.tof_bin_width)) return fail(JP_ERR_ARG, "opts.tof_bin_width must be finite and >= 0");
   int window_bins = (o.tof_bin_width > 0.f && tof_bin) ? o.window_bins : 1;
-  int64_t kpf = 3LL * o.slope_bins * o.offset_bins * window_bins;
+  int64_t kpf = 3LL * o.slope_bins * o.offset_bins * window_bins * o.zoff_bins;
   if (o.flags & JP_PLAN_KEEP_ORDER) kpf = 1;
   if (kpf * (int64_t)n_frames >= (int64_t)kScanTile * kScanTile)
     return fail(JP_ERR_ARG, "too many bins (n_frames * 3 * slope * offset * window >= 2^28)");
@@ -364,7 +393,8 @@ extern "C" int jp_plan_create_batch(jp_plan* out, const float* xs, const float* 
   p->dims.offset_bins = o.offset_bins;
   p->dims.window_bins = window_bins;
   p->dims.keys_per_frame = (int)kpf;
-  p->dims.keys_per_axis = (o.flags & JP_PLAN_KEEP_ORDER) ? 1 : o.slope_bins * o.offset_bins * window_bins;
+  p->dims.zoff_bins = o.zoff_bins;
+  p->dims.keys_per_axis = (o.flags & JP_PLAN_KEEP_ORDER) ? 1 : o.slope_bins * o.offset_bins * window_bins * o.zoff_bins;
   p->ql = quad_layout(*g);
   for (int a = 0; a < 3; ++a)
     if (p->ql.size[a] >= (int64_t)INT32_MAX) {

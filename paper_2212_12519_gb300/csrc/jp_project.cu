@@ -174,13 +174,13 @@ __global__ void __launch_bounds__(kMaxBlock) planned_kernel(const ProjParams p) 
     const int64_t i = (int64_t)tile_s * blockDim.x + threadIdx.x;
     if ((int64_t)tile_s * blockDim.x >= p.n) break;
     if (i >= p.n) continue;
-    const float4 A = __ldg(p.lor + 2 * i);
-    const float4 B = __ldg(p.lor + 2 * i + 1);
+    const float4 A = __ldcs(p.lor + 2 * i);
+    const float4 B = __ldcs(p.lor + 2 * i + 1);
     const float xs[3] = {A.x, A.y, A.z};
     const float xe[3] = {B.x, B.y, B.z};
     const float delta = A.w;
     const int tbin = __float_as_int(B.w);
-    const int64_t j = __ldg(p.perm + i);
+    const int64_t j = __ldcs(p.perm + i);
     const int f = (p.n_frames > 1) ? frame_of(p.frame_off, p.n_frames, i) : 0;
     const int slot = p.shared ? 0 : f;
     Ray r;
@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(kMaxBlock) planned_kernel(const ProjParams p) 
         float* out = p.proj_out + j * (int64_t)N;
         for (int t = 0; t < N; ++t) out[t] = live ? r.w0 * acc[t * blockDim.x] : 0.f;
       } else {
-        p.proj_out[j] = live ? r.w0 * sum : 0.f;
+        __stcs(p.proj_out + j, live ? r.w0 * sum : 0.f);
       }
     } else {
       // ------------------------------ back --------------------------------
@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(kMaxBlock) planned_kernel(const ProjParams p) 
         }
         if (!any) continue;
       } else {
-        val *= __ldg(p.proj_in + j);
+        val *= __ldcs(p.proj_in + j);
         if (val == 0.f) continue;
       }
       for (int k = r.k0; k <= r.k1; ++k) {
@@ -333,16 +333,18 @@ __device__ __forceinline__ float group_sum(float v) {
 
 template <int MODE, bool BACK, bool LUT, int G>
 __global__ void __launch_bounds__(kMaxBlock) group_kernel(const ProjParams p) {
-  static_assert(MODE == 0 || MODE == 2, "group kernel: non-TOF or TOF listmode");
+  static_assert(MODE == 0 || MODE == 2 || (MODE == 1 && BACK),
+                "group kernel: non-TOF, TOF listmode, or TOF-sinogram back projection");
   constexpr int E = 32 / G;  // LORs walked at once per warp
   extern __shared__ float4 smem4[];
   float2* lut = reinterpret_cast<float2*>(smem4);
   const DevTof& T = p.tof;
-  if (MODE == 2 && LUT) {
+  if (MODE != 0 && LUT) {
     build_lut(lut, T);
     __syncthreads();
   }
-  const float inv_h = (MODE == 2) ? (float)(kLut - 1) / (2.f * T.R) : 0.f;
+  const float inv_h = (MODE != 0) ? (float)(kLut - 1) / (2.f * T.R) : 0.f;
+  const int N = T.nbins;
   const int lane = threadIdx.x & 31;
   const int grp = lane / G, gl = lane - grp * G;
   for (;;) {
@@ -354,15 +356,16 @@ __global__ void __launch_bounds__(kMaxBlock) group_kernel(const ProjParams p) {
     const int64_t i = base + lane;
     Ray r;
     r.k0 = 1; r.k1 = 0;
-    float d0 = 0.f, val = 0.f;
+    float d0 = 0.f, val = 0.f, delta = 0.f;
     int slot = 0;
     int32_t j = 0;
     if (i < p.n) {
-      const float4 A = __ldg(p.lor + 2 * i);
-      const float4 B = __ldg(p.lor + 2 * i + 1);
+      const float4 A = __ldcs(p.lor + 2 * i);
+      const float4 B = __ldcs(p.lor + 2 * i + 1);
       const float xs[3] = {A.x, A.y, A.z};
       const float xe[3] = {B.x, B.y, B.z};
-      j = __ldg(p.perm + i);
+      j = __ldcs(p.perm + i);
+      delta = A.w;
       const int f = (p.n_frames > 1) ? frame_of(p.frame_off, p.n_frames, i) : 0;
       slot = p.shared ? 0 : f;
       bool live = ray_setup(xs, xe, p.g, r);
@@ -377,7 +380,7 @@ __global__ void __launch_bounds__(kMaxBlock) group_kernel(const ProjParams p) {
         live = lo <= hi;
       }
       if (BACK && live) {
-        val = r.w0 * __ldg(p.proj_in + j);
+        val = (MODE == 1) ? r.w0 : r.w0 * __ldcs(p.proj_in + j);
         live = val != 0.f;
       }
       if (!live) { r.k0 = 1; r.k1 = 0; r.w0 = 0.f; val = 0.f; }
@@ -398,10 +401,15 @@ __global__ void __launch_bounds__(kMaxBlock) group_kernel(const ProjParams p) {
       const float wc = __shfl_sync(0xffffffffu, r.wc, src);
       const float dw = __shfl_sync(0xffffffffu, r.dw, src);
       const float w0 = __shfl_sync(0xffffffffu, BACK ? val : r.w0, src);
-      float dd0 = 0.f, ddt = 0.f;
+      float dd0 = 0.f, ddt = 0.f, dtc = 0.f, ddl = 0.f;
       if (MODE == 2) {
         dd0 = __shfl_sync(0xffffffffu, d0, src);
         ddt = __shfl_sync(0xffffffffu, r.dt, src);
+      }
+      if (MODE == 1) {
+        ddt = __shfl_sync(0xffffffffu, r.dt, src);
+        dtc = __shfl_sync(0xffffffffu, r.tc, src);
+        ddl = __shfl_sync(0xffffffffu, delta, src);
       }
       const int na = sel3(a, p.g.n[0], p.g.n[1], p.g.n[2]);
       const int nb = (a == 0) ? p.g.n[1] : p.g.n[0];
@@ -437,13 +445,36 @@ __global__ void __launch_bounds__(kMaxBlock) group_kernel(const ProjParams p) {
         {
           float coef = w0;
           if (MODE == 2) coef *= tof_weight<LUT>(lut, fmaf(kk, ddt, dd0), T, inv_h);
+          if (MODE == 1) {
+            // sum over the bins in the window of weight x sinogram value
+            const float* yrow = p.proj_in + (int64_t)jj * N;
+            const float tau = fmaf(kk, ddt, dtc);
+            const float x = (tau - ddl) * T.inv_w + T.hbin;
+            const int t0 = max(0, (int)ceilf(x - T.R_over_w));
+            const int t1 = min(N - 1, (int)floorf(x + T.R_over_w));
+            const float dlo = (tau - ddl) - ((float)t0 - T.hbin) * T.width;
+            float sy = 0.f;
+            if (LUT) {
+              for (int t = t0; t <= t1; ++t)
+                sy = fmaf(lut_g(lut, fmaf(-(float)(t - t0), T.width, dlo), T.R, inv_h), __ldg(yrow + t), sy);
+            } else {
+              float e_hi = erff((dlo + T.half) * T.k);
+              for (int t = t0; t <= t1; ++t) {
+                const float e_lo = erff((fmaf(-(float)(t - t0), T.width, dlo) - T.half) * T.k);
+                sy = fmaf(0.5f * (e_hi - e_lo), __ldg(yrow + t), sy);
+                e_hi = e_lo;
+              }
+            }
+            coef *= sy;
+            if (coef == 0.f) continue;
+          }
           const float ca = (1.f - al) * coef, cb = al * coef;
           atomicAdd(p.quads + qoff + q, make_float4(ca * (1.f - be), cb * (1.f - be), ca * be, cb * be));
         }
       }
       if (!BACK) {
         sum = group_sum<G>(sum);
-        if (gl == 0 && base + src < p.n) p.proj_out[jj] = w0 * sum;
+        if (gl == 0 && base + src < p.n) __stcs(p.proj_out + jj, w0 * sum);
       }
     }
   }
@@ -477,8 +508,8 @@ __global__ void __launch_bounds__(kMaxBlock) osem_kernel(const ProjParams p) {
     r.k0 = 1; r.k1 = 0;
     float d0 = 0.f;
     if (i < p.n) {
-      const float4 A = __ldg(p.lor + 2 * i);
-      const float4 B = __ldg(p.lor + 2 * i + 1);
+      const float4 A = __ldcs(p.lor + 2 * i);
+      const float4 B = __ldcs(p.lor + 2 * i + 1);
       const float xs[3] = {A.x, A.y, A.z};
       const float xe[3] = {B.x, B.y, B.z};
       bool live = ray_setup(xs, xe, p.g, r);
@@ -827,7 +858,7 @@ int launch_planned(const ProjParams& p, int block, cudaStream_t st) {
 template <int MODE, bool BACK, bool LUT, int G>
 int launch_group(const ProjParams& p, int block, cudaStream_t st) {
   auto kern = group_kernel<MODE, BACK, LUT, G>;
-  const size_t smem = (MODE == 2 && LUT) ? kLut * sizeof(float2) : 0;
+  const size_t smem = (MODE != 0 && LUT) ? kLut * sizeof(float2) : 0;
   int per_sm = 0;
   JP_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem));
   if (per_sm < 1) per_sm = 1;
@@ -848,6 +879,16 @@ int launch_group_lpw(const ProjParams& p, int block, int lpw, cudaStream_t st) {
     case 2: return launch_group<MODE, BACK, LUT, 16>(p, block, st);
     case 4: return launch_group<MODE, BACK, LUT, 8>(p, block, st);
     default: return launch_planned<MODE, BACK, LUT>(p, block, st);
+  }
+}
+
+template <bool LUT>
+int launch_sino_back(const ProjParams& p, int block, int lpw, cudaStream_t st) {
+  switch (lpw) {
+    case 1: return launch_group<1, true, LUT, 32>(p, block, st);
+    case 2: return launch_group<1, true, LUT, 16>(p, block, st);
+    case 4: return launch_group<1, true, LUT, 8>(p, block, st);
+    default: return launch_planned<1, true, LUT>(p, block, st);
   }
 }
 
@@ -915,8 +956,8 @@ int planned(jp_plan pl, int mode, bool back, const float* in, float* out, int64_
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t max_quad = std::max(std::max(p.ql.size[0], p.ql.size[1]), p.ql.size[2]);
   int lpw = pl->opts.lors_per_warp;
-  if (lpw == 0) lpw = (mode == 1 || !back) ? 32 : 4;
-  if (mode == 1) lpw = 32;
+  if (lpw == 0) lpw = (!back || mode == 1) ? 32 : 4;
+  if (mode == 1 && !back) lpw = 32;
   p.kfast = (lpw == 32) ? 0 : 1;
   dim3 qgrid(aux_grid(max_quad, 256), slots * 3);
   if (!back) {
@@ -931,8 +972,8 @@ int planned(jp_plan pl, int mode, bool back, const float* in, float* out, int64_
     case 2: rc = launch_group_lpw<0, true, false>(p, block, lpw, st); break;
     case 4: rc = launch_planned<1, false, false>(p, block, st); break;
     case 5: rc = launch_planned<1, false, true>(p, block, st); break;
-    case 6: rc = launch_planned<1, true, false>(p, block, st); break;
-    case 7: rc = launch_planned<1, true, true>(p, block, st); break;
+    case 6: rc = launch_sino_back<false>(p, block, lpw, st); break;
+    case 7: rc = launch_sino_back<true>(p, block, lpw, st); break;
     case 8: rc = launch_group_lpw<2, false, false>(p, block, lpw, st); break;
     case 9: rc = launch_group_lpw<2, false, true>(p, block, lpw, st); break;
     case 10: rc = launch_group_lpw<2, true, false>(p, block, lpw, st); break;
@@ -992,8 +1033,8 @@ __global__ void count_kernel(const ProjParams p, unsigned long long* out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long cnt = 0;
   if (i < p.n) {
-    const float4 A = __ldg(p.lor + 2 * i);
-    const float4 B = __ldg(p.lor + 2 * i + 1);
+    const float4 A = __ldcs(p.lor + 2 * i);
+    const float4 B = __ldcs(p.lor + 2 * i + 1);
     float xs[3] = {A.x, A.y, A.z}, xe[3] = {B.x, B.y, B.z};
     Ray r;
     bool live = ray_setup(xs, xe, p.g, r);
