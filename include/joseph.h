@@ -283,6 +283,13 @@ int jp_back_tof_lm_noalloc(const float* xstart, const float* xend, const int16_t
 int jp_bench_red(float* buf, int64_t n_entries, int32_t per_thread, int32_t iters, float* ms_out,
                  void* stream);
 
+/* Same, with an access pattern: 0 = every lane its own random 16-byte entry
+ * (one 32-byte L2 sector per reduction), 1 = pairs of lanes on the two
+ * halves of one random sector, 2 = a warp on 32 consecutive entries (512
+ * contiguous bytes).  Pattern 0 is jp_bench_red. */
+int jp_bench_red_pattern(float* buf, int64_t n_entries, int32_t per_thread, int32_t iters, int32_t pattern,
+                         float* ms_out, void* stream);
+
 /* thread-local message of the last failing call ("" if none) */
 const char* jp_last_error(void);
 

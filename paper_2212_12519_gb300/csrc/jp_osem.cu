@@ -68,10 +68,18 @@ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
   return x;
 }
 
-__global__ void bench_red_kernel(float4* buf, uint32_t n, int per_thread) {
+__global__ void bench_red_kernel(float4* buf, uint32_t n, int per_thread, int pattern) {
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t lane = threadIdx.x & 31u, warp = t >> 5;
   for (int r = 0; r < per_thread; ++r) {
-    const uint32_t i = mix32(t * 131u + (uint32_t)r) % n;
+    uint32_t i;
+    if (pattern == 1) {
+      i = (mix32((t >> 1) * 131u + (uint32_t)r) % (n / 2)) * 2u + (lane & 1u);
+    } else if (pattern == 2) {
+      i = (mix32(warp * 131u + (uint32_t)r) % (n / 32)) * 32u + lane;
+    } else {
+      i = mix32(t * 131u + (uint32_t)r) % n;
+    }
     atomicAdd(buf + i, make_float4(1.f, 1.f, 1.f, 1.f));
   }
 }
@@ -139,20 +147,28 @@ extern "C" int jp_osem_init(float* x, const float* s, int64_t n, void* stream) {
 
 extern "C" int jp_bench_red(float* buf, int64_t n_entries, int32_t per_thread, int32_t iters, float* ms_out,
                             void* stream) {
+  return jp_bench_red_pattern(buf, n_entries, per_thread, iters, 0, ms_out, stream);
+}
+
+extern "C" int jp_bench_red_pattern(float* buf, int64_t n_entries, int32_t per_thread, int32_t iters,
+                                    int32_t pattern, float* ms_out, void* stream) {
   clear_error();
-  if (!buf || !ms_out || n_entries < 1 || n_entries > (int64_t)UINT32_MAX || per_thread < 1 || iters < 1)
+  if (!buf || !ms_out || n_entries < 64 || n_entries > (int64_t)UINT32_MAX || per_thread < 1 || iters < 1 ||
+      pattern < 0 || pattern > 2)
     return fail(JP_ERR_ARG, "bad arguments");
   if (!aligned(buf, 16)) return fail(JP_ERR_ALIGN, "buf must be 16-byte aligned");
   cudaStream_t st = (cudaStream_t)stream;
   const int blocks = sm_count() * 32, threads = 256;
-  bench_red_kernel<<<blocks, threads, 0, st>>>(reinterpret_cast<float4*>(buf), (uint32_t)n_entries, per_thread);
+  bench_red_kernel<<<blocks, threads, 0, st>>>(reinterpret_cast<float4*>(buf), (uint32_t)n_entries, per_thread,
+                                               pattern);
   count_launch();
   cudaEvent_t a, b;
   JP_TRY_CUDA(cudaEventCreate(&a));
   JP_TRY_CUDA(cudaEventCreate(&b));
   JP_TRY_CUDA(cudaEventRecord(a, st));
   for (int i = 0; i < iters; ++i) {
-    bench_red_kernel<<<blocks, threads, 0, st>>>(reinterpret_cast<float4*>(buf), (uint32_t)n_entries, per_thread);
+    bench_red_kernel<<<blocks, threads, 0, st>>>(reinterpret_cast<float4*>(buf), (uint32_t)n_entries, per_thread,
+                                                 pattern);
     count_launch();
   }
   JP_TRY_CUDA(cudaEventRecord(b, st));

@@ -72,6 +72,7 @@ _SIGS = {
     "jp_osem_init": [P, P, I64, P],
     "jp_back_tof_lm_noalloc": [P, P, P, P, I64, P, P, P, P, P],
     "jp_bench_red": [P, I64, I32, I32, P, P],
+    "jp_bench_red_pattern": [P, I64, I32, I32, I32, P, P],
 }
 
 
@@ -397,17 +398,22 @@ def jp_count_samples(plan: Plan, tof_mode="nontof", tof=None, stream=None) -> in
     return int(out.item())
 
 
-def jp_bench_red(n_entries: int = 3_000_000, per_thread: int = 64, iters: int = 5, stream=None) -> dict:
+def jp_bench_red(n_entries: int = 3_000_000, per_thread: int = 64, iters: int = 5, pattern: int = 0,
+                 stream=None) -> dict:
     """Scattered 16-byte reduction ceiling of the device (measurement helper):
-    reductions per second over an L2-resident buffer of n_entries float4."""
+    reductions per second over an L2-resident buffer of n_entries float4.
+    pattern 0: one random sector per reduction; 1: two reductions per random
+    sector; 2: a warp on 512 contiguous bytes."""
     buf = torch.zeros((n_entries, 4), dtype=torch.float32, device="cuda")
     ms = ctypes.c_float()
-    _check(load().jp_bench_red(_ptr(buf, torch.float32, "buf"), int(n_entries), int(per_thread), int(iters),
-                               ctypes.byref(ms), _stream(stream)))
-    import math
+    _check(load().jp_bench_red_pattern(_ptr(buf, torch.float32, "buf"), int(n_entries), int(per_thread),
+                                       int(iters), int(pattern), ctypes.byref(ms), _stream(stream)))
     blocks = torch.cuda.get_device_properties(buf.device).multi_processor_count * 32
     ops_ = blocks * 256 * per_thread
-    return {"reductions_per_s": ops_ / (ms.value / 1e3), "ms": ms.value, "buffer_bytes": n_entries * 16}
+    sectors_per_red = {0: 1.0, 1: 0.5, 2: 0.5}[int(pattern)]
+    rate = ops_ / (ms.value / 1e3)
+    return {"reductions_per_s": rate, "sectors_per_s": rate * sectors_per_red, "ms": ms.value,
+            "buffer_bytes": n_entries * 16, "pattern": int(pattern)}
 
 
 def jp_launch_count() -> int:

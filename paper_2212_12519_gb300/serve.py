@@ -173,7 +173,7 @@ class OSEMServer:
 # synthetic frame stream
 # ---------------------------------------------------------------------------
 def make_event_pools(tof: synth.TofParams, pool_events: int = 20_000_000, device="cuda", seed: int = 5000):
-    """One pool of TOF listmode events per image size (config-4 recipe):
+    """One pool of TOF listmode events per image size (the listmode batch recipe):
     frames take seeded random windows of their pool."""
     pools = {}
     for k, (geom, ph_spec) in enumerate([(synth.GEOM_OSEM_SMALL, synth.PHANTOM_OSEM_SMALL),
