@@ -259,7 +259,7 @@ def run_ours(args):
     serving = None
     if not args.no_serving and rank == 0:
         rates = [float(r) for r in args.serving_rates.split(",")]
-        serving = run_serving(n_requests=args.serving_requests, rates=rates)
+        serving = run_serving(n_requests=args.serving_requests, rates=rates, max_slots=args.serving_slots)
 
     if rank == 0:
         peaks, peak_kind = measured_peaks()
@@ -496,7 +496,7 @@ def run_profile_case(args):
 # ---------------------------------------------------------------------------
 # served listmode OSEM (frame stream): batched vs sequential plain
 # ---------------------------------------------------------------------------
-def run_serving(n_requests=200, rates=(1.0,), pool_events=20_000_000, max_slots=8, budget_gb=None,
+def run_serving(n_requests=200, rates=(1.0,), pool_events=20_000_000, max_slots=4, budget_gb=None,
                 use_graphs=True, seed=5001):
     from paper_2212_12519_gb300 import osem, serve, synth
     tof = synth.TOF_CLINICAL
@@ -621,13 +621,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=200)
-    ap.add_argument("--serving-rates", default="1.0")
+    ap.add_argument("--serving-rates", default="0.5,1.0,1.5")
     ap.add_argument("--workload", default="tof_lm",
                     choices=["tof_lm", "sino_small", "sino_clinical", "tof_sino", "osem", "profile_case"])
     ap.add_argument("--cpu-lors", type=int, default=200_000)
     ap.add_argument("--budget-gb", type=float, default=None)
     ap.add_argument("--no-graphs", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--serving-slots", type=int, default=4)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -640,7 +641,7 @@ def main():
         jbuild.build()
         ops.load()
         rates = [float(r) for r in args.serving_rates.split(",")]
-        out = run_serving(n_requests=args.serving_requests, rates=rates,
+        out = run_serving(n_requests=args.serving_requests, rates=rates, max_slots=args.serving_slots,
                           budget_gb=args.budget_gb, use_graphs=not args.no_graphs)
         print(json.dumps({"metric": "served listmode OSEM frames/s; p50/p99 latency", "workload": "osem_stream",
                           **out}), flush=True)

@@ -231,6 +231,17 @@ int jp_osem_update(float* x, const float* bp, const float* sens, float scale, in
 int jp_osem_subset_tof_lm(jp_plan p, int32_t f0, int32_t f1, float* x, const float* sens,
                           float sens_scale, float b, const jp_tof* t, void* stream);
 
+/*
+ * jp_osem_subset_tof_lm_dev -- the same subset update, with the background b
+ * read from device memory (float) and the subset's event range read from
+ * the plan's device-side frame offsets when the kernels run.  A launch
+ * sequence captured into a CUDA graph therefore stays valid after the plan
+ * is rebound to another frame's events (up to its capacity) and b is
+ * rewritten: one graph per plan serves every frame.
+ */
+int jp_osem_subset_tof_lm_dev(jp_plan p, int32_t f0, int32_t f1, float* x, const float* sens,
+                              float sens_scale, const float* b_dev, const jp_tof* t, void* stream);
+
 /* listmode OSEM start image: x[j] = sens[j] > 0 ? 1 : 0 for nvox voxels */
 int jp_osem_init(float* x, const float* sens, int64_t nvox, void* stream);
 

@@ -217,6 +217,17 @@ __global__ void scatter_kernel(KeyParams p, const uint32_t* __restrict__ keys, u
   }
 }
 
+// Frame offsets reach the device as kernel arguments (copied at launch), so
+// the host array may be reused as soon as the call returns.
+constexpr int kOffChunk = 256;
+struct OffChunk {
+  int64_t v[kOffChunk];
+};
+
+__global__ void set_offsets_kernel(int64_t* __restrict__ dst, OffChunk c, int count) {
+  for (int i = threadIdx.x; i < count; i += blockDim.x) dst[i] = c.v[i];
+}
+
 // Frame f has LORs with principal axis a iff its keys of axis a hold any LOR.
 // After the scatter, cursor[key] is the end offset of bin `key`.
 __global__ void axis_flags_kernel(const uint32_t* __restrict__ cursor, int n_frames, int keys_per_frame,
@@ -273,8 +284,14 @@ int bind(jp_plan p, const float* xs, const float* xe, const int16_t* tof_bin, co
   } else {
     std::memcpy(p->frame_off_host, off, sizeof(int64_t) * (n_frames + 1));
   }
-  JP_TRY_CUDA(cudaMemcpyAsync(p->frame_off_dev, p->frame_off_host, sizeof(int64_t) * (n_frames + 1),
-                              cudaMemcpyHostToDevice, st));
+  for (int32_t c0 = 0; c0 <= n_frames; c0 += kOffChunk) {
+    OffChunk chunk;
+    const int cnt = std::min<int32_t>(kOffChunk, n_frames + 1 - c0);
+    std::memcpy(chunk.v, p->frame_off_host + c0, sizeof(int64_t) * cnt);
+    set_offsets_kernel<<<1, 256, 0, st>>>(p->frame_off_dev + c0, chunk, cnt);
+    count_launch();
+  }
+  JP_TRY_CUDA(cudaGetLastError());
   p->n = n;
   p->n_frames = n_frames;
   if (n == 0) {

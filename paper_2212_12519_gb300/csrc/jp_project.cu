@@ -96,6 +96,8 @@ struct ProjParams {
   // listmode OSEM subset update
   float4* quads_bp;   // back-projection quads (plane-fastest)
   float bg;           // additive background b
+  const float* bg_ptr;  // or read from device memory when set
+  int f0, f1;         // OSEM: subset frames [f0, f1), range read from frame_off on the device
   const float* sens;  // sensitivity image
   float sens_scale;
   // persistent kernels take chunks of LORs from this counter (reset by the
@@ -498,16 +500,18 @@ __global__ void __launch_bounds__(kMaxBlock) osem_kernel(const ProjParams p) {
   const float inv_h = (float)(kLut - 1) / (2.f * T.R);
   const int lane = threadIdx.x & 31;
   const int grp = lane / G, gl = lane - grp * G;
+  const int64_t start = __ldg(p.frame_off + p.f0), end = __ldg(p.frame_off + p.f1);
+  const float bg = p.bg_ptr ? __ldg(p.bg_ptr) : p.bg;
   for (;;) {
     unsigned int chunk = 0;
     if (lane == 0) chunk = atomicAdd(p.counter, 1u);
-    const int64_t base = (int64_t)__shfl_sync(0xffffffffu, chunk, 0) * 32;
-    if (base >= p.n) break;
+    const int64_t base = start + (int64_t)__shfl_sync(0xffffffffu, chunk, 0) * 32;
+    if (base >= end) break;
     const int64_t i = base + lane;
     Ray r;
     r.k0 = 1; r.k1 = 0;
     float d0 = 0.f;
-    if (i < p.n) {
+    if (i < end) {
       const float4 A = __ldcs(p.lor + 2 * i);
       const float4 B = __ldcs(p.lor + 2 * i + 1);
       const float xs[3] = {A.x, A.y, A.z};
@@ -562,7 +566,7 @@ __global__ void __launch_bounds__(kMaxBlock) osem_kernel(const ProjParams p) {
       }
       sum = group_sum<G>(sum);
       // ratio and back projection of it
-      const float coef0 = (k0 <= k1) ? w0 / fmaf(w0, sum, p.bg) : 0.f;
+      const float coef0 = (k0 <= k1) ? w0 / fmaf(w0, sum, bg) : 0.f;
       for (int k = k0 + gl; k <= k1 && coef0 != 0.f; k += G) {
         const float kk = (float)k - kc;
         const float u = fminf(fmaxf(fmaf(kk, du, uc), -1.f), ub);
@@ -1086,29 +1090,32 @@ extern "C" int jp_count_samples(jp_plan pl, int32_t mode, const jp_tof* t, uint6
   return JP_OK;
 }
 
-extern "C" int jp_osem_subset_tof_lm(jp_plan pl, int32_t f0, int32_t f1, float* x, const float* sens,
-                                     float sens_scale, float b, const jp_tof* t, void* stream) {
+namespace jp {
+namespace {
+int osem_subset(jp_plan pl, int32_t f0, int32_t f1, float* x, const float* sens, float sens_scale, float b,
+                const float* b_dev, const jp_tof* t, void* stream) {
   clear_error();
   if (!pl) return fail(JP_ERR_ARG, "plan is NULL");
   if (!(pl->opts.flags & JP_PLAN_INTERLEAVED)) return fail(JP_ERR_STATE, "OSEM subsets need a JP_PLAN_INTERLEAVED plan");
   if (!pl->has_tof_bin) return fail(JP_ERR_STATE, "TOF listmode needs a plan created with tof_bin");
   if (f0 < 0 || f1 > pl->n_frames || f0 > f1) return fail(JP_ERR_ARG, "frame range outside the plan");
   if (!x || !sens) return fail(JP_ERR_ARG, "x / sens is NULL");
-  if (!aligned(x, 4) || !aligned(sens, 4)) return fail(JP_ERR_ALIGN, "arrays must be 4-byte aligned");
+  if (!aligned(x, 4) || !aligned(sens, 4) || !aligned(b_dev, 4)) return fail(JP_ERR_ALIGN, "arrays must be 4-byte aligned");
   if (!(sens_scale > 0.f) || !isfinite(sens_scale)) return fail(JP_ERR_ARG, "sens_scale must be finite and > 0");
-  if (!(b >= 0.f) || !isfinite(b)) return fail(JP_ERR_ARG, "b must be finite and >= 0");
+  if (!b_dev && (!(b >= 0.f) || !isfinite(b))) return fail(JP_ERR_ARG, "b must be finite and >= 0");
   ProjParams p;
   std::memset(&p, 0, sizeof(p));
   int rc = make_geom(&pl->g, &p.g);
   if (rc) return rc;
   rc = make_tof(t, false, &p.tof);
   if (rc) return rc;
-  const int64_t start = pl->frame_off_host[f0], end = pl->frame_off_host[f1];
-  p.lor = pl->lor + 2 * start;
-  p.perm = pl->perm + start;
+  p.lor = pl->lor;
+  p.perm = pl->perm;
   p.frame_off = pl->frame_off_dev;
   p.n_frames = pl->n_frames;
-  p.n = end - start;
+  p.f0 = f0;
+  p.f1 = f1;
+  p.n = pl->capacity;  // upper bound only; the kernel reads its range on the device
   p.ql = pl->ql;
   p.axis_used = pl->axis_used;
   p.shared = 1;
@@ -1117,6 +1124,7 @@ extern "C" int jp_osem_subset_tof_lm(jp_plan pl, int32_t f0, int32_t f1, float* 
   p.quads = pl->quads;
   p.quads_bp = pl->quads + pl->ql.slot;
   p.bg = b;
+  p.bg_ptr = b_dev;
   p.sens = sens;
   p.sens_scale = sens_scale;
   p.counter = pl->work_counter;
@@ -1132,17 +1140,20 @@ extern "C" int jp_osem_subset_tof_lm(jp_plan pl, int32_t f0, int32_t f1, float* 
     count_launch();
   }
   JP_TRY_CUDA(cudaGetLastError());
-  if (p.n > 0) {
+  if (pl->capacity > 0) {
     const bool lut = !(pl->opts.flags & JP_PLAN_TOF_EXACT);
     int lpw = pl->opts.lors_per_warp;
     if (lpw != 1 && lpw != 2) lpw = 4;
     const int block = std::min(pl->opts.block, kMaxBlock);
     const size_t smem = lut ? kLut * sizeof(float2) : 0;
+    // the event count is known only on the device: size the grid by the
+    // host-side count when it is current, else fill the GPU
+    const int64_t host_n = b_dev ? pl->capacity : pl->frame_off_host[f1] - pl->frame_off_host[f0];
     auto pick = [&](auto kern) -> int {
       int per_sm = 0;
       JP_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem));
       int64_t grid = (int64_t)sm_count() * (per_sm < 1 ? 1 : per_sm);
-      const int64_t need = (p.n + block - 1) / block;
+      const int64_t need = (host_n + block - 1) / block;
       if (grid > need) grid = need;
       kern<<<(unsigned)(grid < 1 ? 1 : grid), block, smem, st>>>(p);
       count_launch();
@@ -1158,6 +1169,22 @@ extern "C" int jp_osem_subset_tof_lm(jp_plan pl, int32_t f0, int32_t f1, float* 
   count_launch();
   JP_TRY_CUDA(cudaGetLastError());
   return JP_OK;
+}
+}  // namespace
+}  // namespace jp
+
+extern "C" int jp_osem_subset_tof_lm(jp_plan pl, int32_t f0, int32_t f1, float* x, const float* sens,
+                                     float sens_scale, float b, const jp_tof* t, void* stream) {
+  return osem_subset(pl, f0, f1, x, sens, sens_scale, b, nullptr, t, stream);
+}
+
+extern "C" int jp_osem_subset_tof_lm_dev(jp_plan pl, int32_t f0, int32_t f1, float* x, const float* sens,
+                                         float sens_scale, const float* b_dev, const jp_tof* t, void* stream) {
+  if (!b_dev) {
+    clear_error();
+    return fail(JP_ERR_ARG, "b_dev is NULL");
+  }
+  return osem_subset(pl, f0, f1, x, sens, sens_scale, 0.f, b_dev, t, stream);
 }
 
 extern "C" int jp_fwd(jp_plan p, const float* img, int64_t s, float* proj, void* st) {

@@ -70,6 +70,7 @@ _SIGS = {
     "jp_count_samples": [P, I32, P, P, P],
     "jp_osem_subset_tof_lm": [P, I32, I32, P, P, F32, F32, P, P],
     "jp_osem_init": [P, P, I64, P],
+    "jp_osem_subset_tof_lm_dev": [P, I32, I32, P, P, F32, P, P, P],
     "jp_back_tof_lm_noalloc": [P, P, P, P, I64, P, P, P, P, P],
     "jp_bench_red": [P, I64, I32, I32, P, P],
     "jp_bench_red_pattern": [P, I64, I32, I32, I32, P, P],
@@ -372,6 +373,18 @@ def jp_osem_subset_tof_lm(plan: Plan, f0: int, f1: int, x, sens, sens_scale: flo
     _check(load().jp_osem_subset_tof_lm(plan.handle, int(f0), int(f1), _ptr(x, torch.float32, "x"),
                                         _ptr(sens, torch.float32, "sens"), float(sens_scale), float(b),
                                         ctypes.byref(t), _stream(stream)))
+    return x
+
+
+def jp_osem_subset_tof_lm_dev(plan: Plan, f0: int, f1: int, x, sens, sens_scale: float, b_dev, tof,
+                              stream=None):
+    """As jp_osem_subset_tof_lm with b in device memory and the subset range
+    read on the device: a captured graph of these calls stays valid when the
+    plan is rebound and b is rewritten."""
+    t = tof_params(tof)
+    _check(load().jp_osem_subset_tof_lm_dev(plan.handle, int(f0), int(f1), _ptr(x, torch.float32, "x"),
+                                            _ptr(sens, torch.float32, "sens"), float(sens_scale),
+                                            _ptr(b_dev, torch.float32, "b"), ctypes.byref(t), _stream(stream)))
     return x
 
 

@@ -62,6 +62,7 @@ class OSEMServer:
         self.admission_waits = 0
         self.peak_bytes = 0
         self.plans: Dict[tuple, ops.Plan] = {}
+        self.slot_graphs: Dict[tuple, "SlotGraph"] = {}
 
     def reserve(self, max_events: int, geoms: List[synth.ImageGeom], n_sub: int = 8):
         """Pre-creates one interleaved plan per (slot, image grid) with room
@@ -82,8 +83,12 @@ class OSEMServer:
                         **self.plan_opts)
                 torch.cuda.synchronize()
                 del xs, tb
+                if self.use_graphs:
+                    self.slot_graphs[(slot, g.shape)] = SlotGraph(
+                        self.plans[(slot, g.shape)], self.sens[g.shape], self.tof, g, n_sub, self.streams[slot])
 
     def close(self):
+        self.slot_graphs.clear()
         for p in self.plans.values():
             p.destroy()
         self.plans.clear()
@@ -92,13 +97,15 @@ class OSEMServer:
         st = self.streams[slot]
         sens = self.sens[req.spec.geom.shape]
         if self.mode == "batched":
-            plan = self.plans.get((slot, req.spec.geom.shape))
-            fr = osem.LMOSEMFrame(req.spec, sens, self.tof, stream=st, plan=plan, **self.plan_opts)
-            if self.use_graphs:
-                fr.run_graph()
+            sg = self.slot_graphs.get((slot, req.spec.geom.shape))
+            if sg is not None:
+                fr = None
+                x = sg.run(req.spec)
             else:
+                plan = self.plans.get((slot, req.spec.geom.shape))
+                fr = osem.LMOSEMFrame(req.spec, sens, self.tof, stream=st, plan=plan, **self.plan_opts)
                 fr.run()
-            x = fr.x
+                x = fr.x
         else:
             fr = None
             with torch.cuda.stream(st):
@@ -167,6 +174,37 @@ class OSEMServer:
                 "mean_ms": float(lat.mean() * 1e3), "makespan_s": makespan,
                 "events_per_s": ev_total * (iters / n) / makespan,
                 "admission_waits": self.admission_waits, "peak_bytes": self.peak_bytes}
+
+
+class SlotGraph:
+    """One OSEM iteration (n_sub subset updates) captured once per slot and
+    image grid, replayed for every frame the slot serves.  The captured
+    kernels read the subset ranges and b from device memory, so rebinding
+    the slot's plan to a new frame keeps the graph valid."""
+
+    def __init__(self, plan: ops.Plan, sens: torch.Tensor, tof: synth.TofParams, geom: synth.ImageGeom,
+                 n_sub: int, stream: torch.cuda.Stream):
+        self.plan, self.sens, self.tof, self.n_sub, self.stream = plan, sens, tof, n_sub, stream
+        self.x = torch.zeros(geom.shape, dtype=torch.float32, device="cuda")
+        self.b = torch.zeros(1, dtype=torch.float32, device="cuda")
+        self.graph = torch.cuda.CUDAGraph()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(self.graph, stream=stream):
+            for m in range(n_sub):
+                ops.jp_osem_subset_tof_lm_dev(plan, m, m + 1, self.x, sens, 1.0 / n_sub, self.b, tof)
+        torch.cuda.synchronize()
+
+    def run(self, spec: osem.FrameSpec) -> torch.Tensor:
+        n = int(spec.xs.shape[0])
+        if spec.n_sub != self.n_sub:
+            raise ValueError("subset count differs from the captured graph")
+        with torch.cuda.stream(self.stream):
+            ops.jp_plan_rebind(self.plan, spec.xs, spec.xe, [0] * spec.n_sub + [n], tof_bin=spec.tof_bin)
+            self.b.fill_(float(spec.b))
+            ops.jp_osem_init(self.x, self.sens)
+            for _ in range(spec.n_iter):
+                self.graph.replay()
+            return self.x.clone()
 
 
 # ---------------------------------------------------------------------------

@@ -77,8 +77,9 @@ def test_serving_alone_equals_mix(ops):
     for shape, pool in pools.items():
         sens[shape] = torch.from_numpy(smooth_sens(pool["geom"], 5201)).cuda()
     reqs = serve.make_requests(pools, 10, rate=1e6, seed=5202, ev_min=2e4, ev_max=1e6)
-    mix = serve.OSEMServer(sens, tof, mode="batched", max_slots=4)
+    mix = serve.OSEMServer(sens, tof, mode="batched", max_slots=4, use_graphs=True)
     mix.reserve(1_000_000, [p["geom"] for p in pools.values()])
+    assert len(mix.slot_graphs) == 8
     st = mix.run(reqs)
     assert st["requests"] == 10
     x_mix = [r.x.clone() for r in reqs]
