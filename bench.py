@@ -4,8 +4,8 @@ Workload (default): 8 images of 200x200x71 voxels (2 mm), 40M synthetic TOF
 listmode events each (320M events), clinical scanner (36 rings x 672
 crystals, R = 400 mm), 29 TOF bins of 28 mm, FWHM 57.7 mm, 3 sigma.  One
 step = sort/pack all events into the plan (binning) + forward projection of
-the batch through the autograd Function + the loss sum(w log(Ax + b)) + its
-backward (the adjoint kernel).  events/s = events in the batch / step time.
+the batch through the autograd Function + the loss sum(w log(Ax + b)) (fused
+value / gradient kernels) + its backward (the adjoint kernel).  events/s = events in the batch / step time.
 
 Usage: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 Under torchrun each rank runs its own batch (weak scaling, no collective on
@@ -142,8 +142,9 @@ def make_tof_lm_batch(rank: int, n_frames: int, events: int, device):
     bvec = torch.repeat_interleave(torch.tensor(bvals, dtype=torch.float32, device=device),
                                    torch.full((n_frames,), events, device=device))
     x = torch.stack(imgs).contiguous()
+    bframe = torch.tensor(bvals, dtype=torch.float32, device=device)
     return dict(geom=g, tof=tof, xs=xs.contiguous(), xe=xe.contiguous(), tb=tb.contiguous(),
-                w=w, bvec=bvec.contiguous(), x=x, offsets=offsets, bvals=bvals)
+                w=w, bvec=bvec.contiguous(), bframe=bframe, x=x, offsets=offsets, bvals=bvals)
 
 
 # ---------------------------------------------------------------------------
@@ -152,7 +153,7 @@ def make_tof_lm_batch(rank: int, n_frames: int, events: int, device):
 def run_ours(args):
     import torch.distributed as dist
     from paper_2212_12519_gb300 import ops
-    from paper_2212_12519_gb300.autograd import JosephTOFLM
+    from paper_2212_12519_gb300.autograd import JosephTOFLM, PoissonLogLik
     from paper_2212_12519_gb300 import build as jbuild
 
     ws, rank, local = dist_env()
@@ -205,7 +206,7 @@ def run_ours(args):
             ops.jp_plan_rebind(plan, W["xs"], W["xe"], W["offsets"], tof_bin=W["tb"])
         x.grad = None
         p = TimedTOFLM.apply(x) if record else JosephTOFLM.apply(x, plan, tof)
-        loss = (W["w"] * torch.log(p + W["bvec"])).sum()
+        loss = PoissonLogLik.apply(p, plan, W["w"], W["bframe"])
         loss.backward()
         return loss
 
@@ -309,13 +310,13 @@ def run_e2e(args, W, plan, g, tof, dev, ws):
     """Same step through the public API, inputs from pinned host memory and
     the loss + gradient images read back every step."""
     from paper_2212_12519_gb300 import ops
-    from paper_2212_12519_gb300.autograd import JosephTOFLM
-    host = {k: W[k].cpu().pin_memory() for k in ("xs", "xe", "tb", "w", "bvec", "x")}
+    from paper_2212_12519_gb300.autograd import JosephTOFLM, PoissonLogLik
+    host = {k: W[k].cpu().pin_memory() for k in ("xs", "xe", "tb", "w", "bframe", "x")}
     dbuf = {k: torch.empty_like(W[k]) for k in host}
     out_grad = torch.empty(W["x"].shape, dtype=torch.float32).pin_memory()
-    out_loss = torch.empty((), dtype=torch.float32).pin_memory()
+    out_loss = torch.empty((), dtype=torch.float64).pin_memory()
     h2d = sum(v.numel() * v.element_size() for v in host.values())
-    d2h = out_grad.numel() * 4 + 4
+    d2h = out_grad.numel() * 4 + 8
     stream = torch.cuda.current_stream()
 
     def step():
@@ -324,7 +325,7 @@ def run_e2e(args, W, plan, g, tof, dev, ws):
         ops.jp_plan_rebind(plan, dbuf["xs"], dbuf["xe"], W["offsets"], tof_bin=dbuf["tb"])
         x = dbuf["x"].requires_grad_(True)
         p = JosephTOFLM.apply(x, plan, tof)
-        loss = (dbuf["w"] * torch.log(p + dbuf["bvec"])).sum()
+        loss = PoissonLogLik.apply(p, plan, dbuf["w"], dbuf["bframe"])
         loss.backward()
         out_grad.copy_(x.grad, non_blocking=True)
         out_loss.copy_(loss.detach(), non_blocking=True)

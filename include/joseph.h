@@ -242,6 +242,20 @@ int jp_osem_subset_tof_lm(jp_plan p, int32_t f0, int32_t f1, float* x, const flo
 int jp_osem_subset_tof_lm_dev(jp_plan p, int32_t f0, int32_t f1, float* x, const float* sens,
                               float sens_scale, const float* b_dev, const jp_tof* t, void* stream);
 
+/*
+ * Listmode Poisson log-likelihood of a forward projection p (the training
+ * objective of unrolled reconstruction networks, paper Sec. 4):
+ *   jp_poisson_loglik_value: *value (device double) = sum_e w_e log(p_e + b_f)
+ *   jp_poisson_loglik_grad:  grad_e = scale * w_e / (p_e + b_f)
+ * w may be NULL (all ones); b is device float [n_frames] with b_f the
+ * background of event e's frame (frames from the plan's offsets in caller
+ * order; plan NULL: one frame); scale is a device double or NULL (1).
+ */
+int jp_poisson_loglik_value(jp_plan p, const float* proj, const float* w, const float* b, int64_t n,
+                            double* value, void* stream);
+int jp_poisson_loglik_grad(jp_plan p, const float* proj, const float* w, const float* b, const double* scale,
+                           int64_t n, float* grad, void* stream);
+
 /* listmode OSEM start image: x[j] = sens[j] > 0 ? 1 : 0 for nvox voxels */
 int jp_osem_init(float* x, const float* sens, int64_t nvox, void* stream);
 

@@ -50,3 +50,26 @@ def tof_lm_project(x, plan, tof):
 
 def nontof_project(x, plan):
     return JosephNonTOF.apply(x, plan)
+
+
+class PoissonLogLik(torch.autograd.Function):
+    """L = sum_e w_e log(p_e + b_f) for listmode projections p (FP64 sum),
+    value and gradient each in one pass of the library's kernels; b holds one
+    background per frame of ``plan`` (or one value with plan None)."""
+
+    @staticmethod
+    def forward(ctx, p, plan, w, b):
+        p = p.contiguous()
+        ctx.save_for_backward(p)
+        ctx.plan, ctx.w, ctx.b = plan, w, b
+        return ops.jp_poisson_loglik_value(plan, p, w, b)
+
+    @staticmethod
+    def backward(ctx, gout):
+        (p,) = ctx.saved_tensors
+        g = ops.jp_poisson_loglik_grad(ctx.plan, p, ctx.w, ctx.b, scale=gout.to(torch.float64).contiguous())
+        return g, None, None, None
+
+
+def poisson_loglik(p, plan, w, b):
+    return PoissonLogLik.apply(p, plan, w, b)

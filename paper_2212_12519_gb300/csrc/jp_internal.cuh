@@ -286,8 +286,9 @@ struct jp_plan_s {
   jp_plan_opts opts;
   jp::PlanDims dims;
   bool has_tof_bin, has_delta;
-  float4* lor;            // [2*capacity]: (xs, delta), (xe, tof_bin bits)
-  int32_t* perm;          // [capacity] binned position -> caller index
+  float4* lor;            // [2*capacity]: (xs, delta or caller index bits), (xe, tof_bin bits)
+  int32_t* perm;          // [capacity] binned position -> caller index (used when delta is given;
+                          // otherwise the caller index rides in the record's first .w)
   uint32_t* keys;         // [capacity]
   uint32_t* hist;         // [frame_capacity * keys_per_frame + 1]
   uint32_t* block_sums;   // scan scratch

@@ -42,6 +42,37 @@ __global__ void update_kernel(float* __restrict__ x, const float* __restrict__ b
   }
 }
 
+__global__ void loglik_value_kernel(const float* __restrict__ p, const float* __restrict__ w,
+                                    const float* __restrict__ b, const int64_t* __restrict__ off, int n_frames,
+                                    int64_t n, double* out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int f = (n_frames > 1) ? frame_of(off, n_frames, i) : 0;
+    const float wi = w ? __ldcs(w + i) : 1.f;
+    s += (double)(wi * logf(__ldcs(p + i) + __ldg(b + f)));
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) atomicAdd(out, s);
+  }
+}
+
+__global__ void loglik_grad_kernel(const float* __restrict__ p, const float* __restrict__ w,
+                                   const float* __restrict__ b, const int64_t* __restrict__ off, int n_frames,
+                                   const double* __restrict__ scale, int64_t n, float* __restrict__ g) {
+  const float sc = scale ? (float)__ldg(scale) : 1.f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int f = (n_frames > 1) ? frame_of(off, n_frames, i) : 0;
+    const float wi = w ? __ldcs(w + i) : 1.f;
+    __stcs(g + i, sc * wi / (__ldcs(p + i) + __ldg(b + f)));
+  }
+}
+
 __global__ void init_kernel(float* __restrict__ x, const float* __restrict__ s, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     x[i] = s[i] > 0.f ? 1.f : 0.f;
@@ -129,6 +160,56 @@ extern "C" int jp_osem_update(float* x, const float* bp, const float* s, float s
   if (total == 0) return JP_OK;
   update_kernel<<<grid_for(total, 256), 256, 0, (cudaStream_t)stream>>>(x, bp, s, scale, nvox, n_frames,
                                                                        stride, s_stride);
+  count_launch();
+  JP_TRY_CUDA(cudaGetLastError());
+  return JP_OK;
+}
+
+namespace {
+int loglik_common(jp_plan pl, const float* p, const float* w, const float* b, int64_t n, const int64_t** off,
+                  int* nf) {
+  if (n < 0) return fail(JP_ERR_ARG, "n must be >= 0");
+  if (n > 0 && (!p || !b)) return fail(JP_ERR_ARG, "NULL pointer");
+  if (!aligned(p, 4) || !aligned(w, 4) || !aligned(b, 4)) return fail(JP_ERR_ALIGN, "misaligned array");
+  *off = nullptr;
+  *nf = 1;
+  if (pl) {
+    if (pl->n != n) return fail(JP_ERR_ARG, "n does not match the plan");
+    if (pl->opts.flags & JP_PLAN_INTERLEAVED) return fail(JP_ERR_STATE, "frames of an interleaved plan are not contiguous");
+    *off = pl->frame_off_dev;
+    *nf = pl->n_frames;
+  }
+  return JP_OK;
+}
+}  // namespace
+
+extern "C" int jp_poisson_loglik_value(jp_plan pl, const float* p, const float* w, const float* b, int64_t n,
+                                       double* value, void* stream) {
+  clear_error();
+  if (!value || !aligned(value, 8)) return fail(JP_ERR_ARG, "value must be an aligned device double");
+  const int64_t* off;
+  int nf;
+  int rc = loglik_common(pl, p, w, b, n, &off, &nf);
+  if (rc) return rc;
+  JP_TRY_CUDA(cudaMemsetAsync(value, 0, sizeof(double), (cudaStream_t)stream));
+  if (n == 0) return JP_OK;
+  loglik_value_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(p, w, b, off, nf, n, value);
+  count_launch();
+  JP_TRY_CUDA(cudaGetLastError());
+  return JP_OK;
+}
+
+extern "C" int jp_poisson_loglik_grad(jp_plan pl, const float* p, const float* w, const float* b,
+                                      const double* scale, int64_t n, float* grad, void* stream) {
+  clear_error();
+  if (n > 0 && !grad) return fail(JP_ERR_ARG, "grad is NULL");
+  if (!aligned(grad, 4) || !aligned(scale, 8)) return fail(JP_ERR_ALIGN, "misaligned array");
+  const int64_t* off;
+  int nf;
+  int rc = loglik_common(pl, p, w, b, n, &off, &nf);
+  if (rc) return rc;
+  if (n == 0) return JP_OK;
+  loglik_grad_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(p, w, b, off, nf, scale, n, grad);
   count_launch();
   JP_TRY_CUDA(cudaGetLastError());
   return JP_OK;

@@ -209,11 +209,13 @@ __global__ void scatter_kernel(KeyParams p, const uint32_t* __restrict__ keys, u
   for (int q = 0; q < kScatterPer; ++q) {
     const int64_t j = base + (int64_t)q * blockDim.x;
     if (j >= p.n) continue;
-    const float dl = p.delta ? p.delta[j] : 0.f;
+    // without TOF centre offsets the caller index rides in the record, so a
+    // LOR costs one scattered 32-byte sector instead of two
+    const float w0 = p.delta ? p.delta[j] : __int_as_float((int)j);
     const int tb = p.tof_bin ? (int)p.tof_bin[j] : 0;
-    lor[2 * (int64_t)pos[q]] = make_float4(p.xs[3 * j], p.xs[3 * j + 1], p.xs[3 * j + 2], dl);
+    lor[2 * (int64_t)pos[q]] = make_float4(p.xs[3 * j], p.xs[3 * j + 1], p.xs[3 * j + 2], w0);
     lor[2 * (int64_t)pos[q] + 1] = make_float4(p.xe[3 * j], p.xe[3 * j + 1], p.xe[3 * j + 2], __int_as_float(tb));
-    perm[pos[q]] = (int32_t)j;
+    if (p.delta) perm[pos[q]] = (int32_t)j;
   }
 }
 
@@ -478,6 +480,15 @@ extern "C" int jp_plan_destroy(jp_plan p) {
   return JP_OK;
 }
 
+namespace jp {
+namespace {
+__global__ void perm_from_records(const float4* __restrict__ lor, int64_t n, int32_t* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = __float_as_int(lor[2 * i].w);
+}
+}  // namespace
+}  // namespace jp
+
 extern "C" int jp_plan_info(jp_plan p, int64_t* n_lor, int32_t* n_frames, int32_t* perm_out,
                             void* stream) {
   clear_error();
@@ -486,8 +497,16 @@ extern "C" int jp_plan_info(jp_plan p, int64_t* n_lor, int32_t* n_frames, int32_
   if (n_frames) *n_frames = p->n_frames;
   if (perm_out && p->n > 0) {
     if (!aligned(perm_out, 4)) return fail(JP_ERR_ALIGN, "perm_out must be 4-byte aligned");
-    JP_TRY_CUDA(cudaMemcpyAsync(perm_out, p->perm, sizeof(int32_t) * p->n, cudaMemcpyDeviceToDevice,
-                                (cudaStream_t)stream));
+    if (p->has_delta) {
+      JP_TRY_CUDA(cudaMemcpyAsync(perm_out, p->perm, sizeof(int32_t) * p->n, cudaMemcpyDeviceToDevice,
+                                  (cudaStream_t)stream));
+    } else {
+      int64_t g = (p->n + 255) / 256;
+      if (g > (int64_t)sm_count() * 8) g = (int64_t)sm_count() * 8;
+      perm_from_records<<<(unsigned)g, 256, 0, (cudaStream_t)stream>>>(p->lor, p->n, perm_out);
+      count_launch();
+      JP_TRY_CUDA(cudaGetLastError());
+    }
   }
   return JP_OK;
 }

@@ -100,6 +100,7 @@ struct ProjParams {
   int f0, f1;         // OSEM: subset frames [f0, f1), range read from frame_off on the device
   const float* sens;  // sensitivity image
   float sens_scale;
+  int perm_in_rec;    // caller index in the first record's .w (no TOF centre offsets)
   // persistent kernels take chunks of LORs from this counter (reset by the
   // workspace kernel launched just before them), so the chunks in flight
   // stay a contiguous window of the binned order (one frame's image at a time)
@@ -180,9 +181,9 @@ __global__ void __launch_bounds__(kMaxBlock) planned_kernel(const ProjParams p) 
     const float4 B = __ldcs(p.lor + 2 * i + 1);
     const float xs[3] = {A.x, A.y, A.z};
     const float xe[3] = {B.x, B.y, B.z};
-    const float delta = A.w;
+    const float delta = p.perm_in_rec ? 0.f : A.w;
     const int tbin = __float_as_int(B.w);
-    const int64_t j = __ldcs(p.perm + i);
+    const int64_t j = p.perm_in_rec ? (int64_t)__float_as_int(A.w) : (int64_t)__ldcs(p.perm + i);
     const int f = (p.n_frames > 1) ? frame_of(p.frame_off, p.n_frames, i) : 0;
     const int slot = p.shared ? 0 : f;
     Ray r;
@@ -366,13 +367,13 @@ __global__ void __launch_bounds__(kMaxBlock) group_kernel(const ProjParams p) {
       const float4 B = __ldcs(p.lor + 2 * i + 1);
       const float xs[3] = {A.x, A.y, A.z};
       const float xe[3] = {B.x, B.y, B.z};
-      j = __ldcs(p.perm + i);
-      delta = A.w;
+      j = p.perm_in_rec ? __float_as_int(A.w) : __ldcs(p.perm + i);
+      delta = p.perm_in_rec ? 0.f : A.w;
       const int f = (p.n_frames > 1) ? frame_of(p.frame_off, p.n_frames, i) : 0;
       slot = p.shared ? 0 : f;
       bool live = ray_setup(xs, xe, p.g, r);
       if (MODE == 2 && live) {
-        const float c = (float)__float_as_int(B.w) * T.width + A.w;
+        const float c = (float)__float_as_int(B.w) * T.width + delta;
         d0 = r.tc - c;
         const float t1 = (-T.R - d0) / r.dt, t2 = (T.R - d0) / r.dt;
         const float lo = fmaxf(ceilf(r.kc + fminf(t1, t2)), (float)r.k0);
@@ -518,7 +519,7 @@ __global__ void __launch_bounds__(kMaxBlock) osem_kernel(const ProjParams p) {
       const float xe[3] = {B.x, B.y, B.z};
       bool live = ray_setup(xs, xe, p.g, r);
       if (live) {
-        const float c = (float)__float_as_int(B.w) * T.width + A.w;
+        const float c = (float)__float_as_int(B.w) * T.width + (p.perm_in_rec ? 0.f : A.w);
         d0 = r.tc - c;
         const float t1 = (-T.R - d0) / r.dt, t2 = (T.R - d0) / r.dt;
         const float lo = fmaxf(ceilf(r.kc + fminf(t1, t2)), (float)r.k0);
@@ -952,6 +953,7 @@ int planned(jp_plan pl, int mode, bool back, const float* in, float* out, int64_
   p.axis_used = pl->axis_used;
   p.shared = (img_stride == 0 || pl->n_frames == 1) ? 1 : 0;
   p.counter = pl->work_counter;
+  p.perm_in_rec = pl->has_delta ? 0 : 1;
   if (back) { p.proj_in = in; p.img_out = out; } else { p.img_in = in; p.proj_out = out; }
   const int slots = p.shared ? 1 : pl->n_frames;
   if (slots * 3 > 65535) return fail(JP_ERR_ARG, "too many frames with distinct images (max 21845)");
@@ -1043,7 +1045,7 @@ __global__ void count_kernel(const ProjParams p, unsigned long long* out) {
     Ray r;
     bool live = ray_setup(xs, xe, p.g, r);
     if (live && MODE == 2) {
-      const float c = (float)__float_as_int(B.w) * p.tof.width + A.w;
+      const float c = (float)__float_as_int(B.w) * p.tof.width + (p.perm_in_rec ? 0.f : A.w);
       const float d0 = r.tc - c;
       const float t1 = (-p.tof.R - d0) / r.dt, t2 = (p.tof.R - d0) / r.dt;
       const float lo = fmaxf(ceilf(r.kc + fminf(t1, t2)), (float)r.k0);
@@ -1079,6 +1081,7 @@ extern "C" int jp_count_samples(jp_plan pl, int32_t mode, const jp_tof* t, uint6
   }
   p.lor = pl->lor;
   p.n = pl->n;
+  p.perm_in_rec = pl->has_delta ? 0 : 1;
   cudaStream_t st = (cudaStream_t)stream;
   JP_TRY_CUDA(cudaMemsetAsync(out, 0, sizeof(uint64_t), st));
   if (p.n == 0) return JP_OK;
@@ -1128,6 +1131,7 @@ int osem_subset(jp_plan pl, int32_t f0, int32_t f1, float* x, const float* sens,
   p.sens = sens;
   p.sens_scale = sens_scale;
   p.counter = pl->work_counter;
+  p.perm_in_rec = pl->has_delta ? 0 : 1;
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t max_quad = std::max(std::max(p.ql.size[0], p.ql.size[1]), p.ql.size[2]);
   dim3 qgrid(aux_grid(max_quad, 256), 3);

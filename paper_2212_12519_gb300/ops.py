@@ -71,6 +71,8 @@ _SIGS = {
     "jp_osem_subset_tof_lm": [P, I32, I32, P, P, F32, F32, P, P],
     "jp_osem_init": [P, P, I64, P],
     "jp_osem_subset_tof_lm_dev": [P, I32, I32, P, P, F32, P, P, P],
+    "jp_poisson_loglik_value": [P, P, P, P, I64, P, P],
+    "jp_poisson_loglik_grad": [P, P, P, P, P, I64, P, P],
     "jp_back_tof_lm_noalloc": [P, P, P, P, I64, P, P, P, P, P],
     "jp_bench_red": [P, I64, I32, I32, P, P],
     "jp_bench_red_pattern": [P, I64, I32, I32, I32, P, P],
@@ -386,6 +388,25 @@ def jp_osem_subset_tof_lm_dev(plan: Plan, f0: int, f1: int, x, sens, sens_scale:
                                             _ptr(sens, torch.float32, "sens"), float(sens_scale),
                                             _ptr(b_dev, torch.float32, "b"), ctypes.byref(t), _stream(stream)))
     return x
+
+
+def jp_poisson_loglik_value(plan: Optional[Plan], proj, w, b, out=None, stream=None):
+    """sum_e w_e log(p_e + b_frame(e)) as a device double (0-dim tensor)."""
+    out = torch.empty((), dtype=torch.float64, device=proj.device) if out is None else out
+    _check(load().jp_poisson_loglik_value(plan.handle if plan is not None else None, _ptr(proj, torch.float32, "proj"),
+                                          _ptr(w, torch.float32, "w"), _ptr(b, torch.float32, "b"), int(proj.numel()),
+                                          _ptr(out, torch.float64, "value"), _stream(stream)))
+    return out
+
+
+def jp_poisson_loglik_grad(plan: Optional[Plan], proj, w, b, scale=None, out=None, stream=None):
+    """grad_e = scale * w_e / (p_e + b_frame(e)) (scale: device double or None)."""
+    out = torch.empty_like(proj) if out is None else out
+    _check(load().jp_poisson_loglik_grad(plan.handle if plan is not None else None, _ptr(proj, torch.float32, "proj"),
+                                         _ptr(w, torch.float32, "w"), _ptr(b, torch.float32, "b"),
+                                         _ptr(scale, torch.float64, "scale"), int(proj.numel()),
+                                         _ptr(out, torch.float32, "grad"), _stream(stream)))
+    return out
 
 
 def jp_osem_init(x, sens, stream=None):

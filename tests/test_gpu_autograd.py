@@ -82,3 +82,31 @@ def test_torch_gradcheck_double_adjoint(ops):
     lhs = float((p.double() * y.double()).sum())
     rhs = float((x.detach().double() * gx.double()).sum())
     assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+
+
+def test_fused_poisson_loglik_vs_oracle(ops):
+    """The fused log-likelihood Function (value and gradient kernels) with
+    the projector: value and image gradient against the FP64 oracle, per
+    frame backgrounds from the plan's frames."""
+    from paper_2212_12519_gb300.autograd import JosephTOFLM, PoissonLogLik
+    tof = synth.TOF_CLINICAL
+    probs = [crop_problem(seed=4500 + 10 * k, n=6000 + 500 * k) for k in range(2)]
+    g = probs[0][0]
+    xs = torch.cat([p[2] for p in probs]).cuda()
+    xe = torch.cat([p[3] for p in probs]).cuda()
+    tb = torch.cat([p[4] for p in probs]).cuda()
+    w = torch.cat([p[5] for p in probs]).cuda()
+    off = np.cumsum([0] + [p[2].shape[0] for p in probs]).tolist()
+    bvals = [0.3, 0.7]
+    plan = ops.jp_plan_create_batch(xs, xe, g, off, tof_bin=tb, tof_bin_width=tof.bin_width)
+    x = torch.stack([p[1] + 0.1 for p in probs]).cuda().requires_grad_(True)
+    loss = PoissonLogLik.apply(JosephTOFLM.apply(x, plan, tof), plan, w,
+                               torch.tensor(bvals, dtype=torch.float32, device="cuda"))
+    loss.backward()
+    tot = 0.0
+    for k, pr in enumerate(probs):
+        f_or, g_or = oracle.poisson_loglik_grad((pr[1] + 0.1).numpy(), pr[2].numpy(), pr[3].numpy(), pr[4].numpy(),
+                                                g, tof, pr[5].numpy(), bvals[k])
+        tot += f_or
+        assert rel_l2(x.grad[k].cpu().numpy(), g_or) <= 1e-4
+    assert float(loss) == pytest.approx(tot, rel=1e-5)
