@@ -473,6 +473,30 @@ def run_sino(args):
 # (launch order: plan [key, scan x3, scatter, flags], then twice
 # [quad build, forward, quad zero, back, fold-back], then a rebind)
 # ---------------------------------------------------------------------------
+def run_profile_osem(args):
+    """One served frame (--events events, 200x200x71), 3 iterations x 8
+    subsets through direct launches, for the ncu launch list."""
+    from paper_2212_12519_gb300 import build as jbuild, ops, osem, synth
+    jbuild.build()
+    ops.load()
+    dev = torch.device("cuda")
+    g, tof = synth.GEOM_CLINICAL, synth.TOF_CLINICAL
+    ph = synth.ellipsoid_phantom(g, synth.PHANTOM_CLINICAL, 5010, device=dev)
+    xs, xe, tb = synth.lm_events(ph, g, synth.SCANNER_CLINICAL, tof, args.events, seed=5011, device=dev)
+    sens = torch.ones(g.shape, device=dev)
+    spec = osem.FrameSpec(xs, xe, tb, g, synth.background_level(ph, tof))
+    fr = osem.LMOSEMFrame(spec, sens, tof)
+    fr.run()
+    torch.cuda.synchronize()
+    rng = torch.cuda.nvtx.range_start("timed")
+    t0 = time.perf_counter()
+    fr = osem.LMOSEMFrame(spec, sens, tof, plan=fr.plan)
+    fr.run()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_end(rng)
+    print(json.dumps({"profile_osem": args.events, "ms": (time.perf_counter() - t0) * 1e3}))
+
+
 def run_profile_case(args):
     from paper_2212_12519_gb300 import build as jbuild, ops, synth
     jbuild.build()
@@ -624,7 +648,8 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=200)
     ap.add_argument("--serving-rates", default="0.5,1.0,1.5")
     ap.add_argument("--workload", default="tof_lm",
-                    choices=["tof_lm", "sino_small", "sino_clinical", "tof_sino", "osem", "profile_case"])
+                    choices=["tof_lm", "sino_small", "sino_clinical", "tof_sino", "osem", "profile_case",
+                             "profile_osem"])
     ap.add_argument("--cpu-lors", type=int, default=200_000)
     ap.add_argument("--budget-gb", type=float, default=None)
     ap.add_argument("--no-graphs", action="store_true")
@@ -635,6 +660,8 @@ def main():
         run_reference(args)
     elif args.workload == "profile_case":
         run_profile_case(args)
+    elif args.workload == "profile_osem":
+        run_profile_osem(args)
     elif args.workload in SINO_WORKLOADS:
         run_sino(args)
     elif args.workload == "osem":

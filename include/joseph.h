@@ -90,7 +90,7 @@ typedef struct {
   int32_t slope_bins;     /* bins over the in-plane slope d_b/d_a in [-1,1] (0 = 128) */
   int32_t offset_bins;    /* bins over the in-plane offset at the central plane (0 = 256) */
   int32_t window_bins;    /* bins over the TOF-window centre along the principal
-                             axis, listmode plans only (0 = 64); n_frames * 3 * slope *
+                             axis, listmode plans only (0 = 16); n_frames * 3 * slope *
                              offset * window * zoff must stay below 2^28 */
   float tof_bin_width;    /* mm; > 0 with tof_bin given: bin listmode events by
                              their TOF window centre; 0 = ignore */
@@ -102,7 +102,7 @@ typedef struct {
                              instead of the interpolated table (see below) */
   int32_t zoff_bins;      /* bins over the offset along axis c (the fastest image
                              axis for principal axes 0 and 1) at the central plane,
-                             the last (fastest) key field (0 = 1: not binned) */
+                             the last (fastest) key field (0 = 8; 1 = not binned) */
 } jp_plan_opts;
 
 #define JP_PLAN_KEEP_ORDER 1

@@ -19,10 +19,10 @@ from typing import Callable, Dict, List, Optional
 import torch
 
 CANDIDATES: List[dict] = [
-    dict(block=b, lors_per_warp=l, slope_bins=s, offset_bins=o, window_bins=w)
+    dict(block=b, lors_per_warp=l, slope_bins=s, offset_bins=o, window_bins=w, zoff_bins=z)
     for b in (256, 512)
     for l in (0, 4, 32)
-    for (s, o, w) in ((128, 256, 64), (64, 64, 16), (256, 128, 32))
+    for (s, o, w, z) in ((128, 256, 16, 8), (128, 256, 64, 1), (128, 256, 32, 4), (64, 64, 16, 1))
 ]
 
 _lock = threading.Lock()

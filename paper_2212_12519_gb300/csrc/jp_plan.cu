@@ -388,8 +388,8 @@ extern "C" int jp_plan_create_batch(jp_plan* out, const float* xs, const float* 
   if (o.block < 64 || o.block > 512 || (o.block % 32) != 0) return fail(JP_ERR_ARG, "opts.block must be 64..512, multiple of 32");
   if (o.slope_bins == 0) o.slope_bins = 128;
   if (o.offset_bins == 0) o.offset_bins = 256;
-  if (o.window_bins == 0) o.window_bins = 64;
-  if (o.zoff_bins == 0) o.zoff_bins = 1;
+  if (o.window_bins == 0) o.window_bins = 16;
+  if (o.zoff_bins == 0) o.zoff_bins = 8;
   if (o.slope_bins < 1 || o.offset_bins < 1 || o.window_bins < 1 || o.zoff_bins < 1)
     return fail(JP_ERR_ARG, "bin counts must be >= 1");
   if (o.lors_per_warp != 0 && o.lors_per_warp != 1 && o.lors_per_warp != 2 && o.lors_per_warp != 4 &&

@@ -45,6 +45,11 @@ def sensitivity(geom: synth.ImageGeom, spec: synth.SinoSpec = synth.SINO_CLINICA
     return s, info
 
 
+# Sort granularity of a frame's subset plan: the subsets multiply the key
+# space, so coarser bins than a single-frame plan keep the histogram small.
+OSEM_PLAN_OPTS = dict(slope_bins=64, offset_bins=128, window_bins=16, zoff_bins=4)
+
+
 @dataclass
 class FrameSpec:
     """One listmode frame: events on the device plus its reconstruction setup."""
@@ -71,9 +76,11 @@ class LMOSEMFrame:
         n = int(spec.xs.shape[0])
         with torch.cuda.stream(self.stream):
             if plan is None:
+                opts = dict(OSEM_PLAN_OPTS)
+                opts.update(plan_opts)
                 self.plan = ops.jp_plan_create_subsets(spec.xs, spec.xe, spec.geom, spec.n_sub,
                                                        tof_bin=spec.tof_bin, tof_bin_width=tof.bin_width,
-                                                       **plan_opts)
+                                                       **opts)
             else:
                 if plan.n_frames != spec.n_sub and plan.frame_offsets is None:
                     raise ValueError("plan/subset mismatch")
@@ -132,13 +139,13 @@ class LMOSEMFrame:
 
 
 def estimate_bytes(n_events: int, geom: synth.ImageGeom, n_sub: int = 8,
-                   slope_bins=128, offset_bins=256, window_bins=64) -> int:
+                   slope_bins=64, offset_bins=128, window_bins=16, zoff_bins=4) -> int:
     """Device bytes a frame holds while it is being reconstructed: its
     events, its plan (packed events, permutation, keys, histogram) and the
     image workspace."""
     n0, n1, n2 = geom.shape
     quad = 16 * (n0 * (n1 + 2) * (n2 + 2) + n1 * (n0 + 2) * (n2 + 2) + n2 * (n0 + 2) * (n1 + 2))
-    hist = 4 * n_sub * 3 * slope_bins * offset_bins * window_bins
+    hist = 4 * n_sub * 3 * slope_bins * offset_bins * window_bins * zoff_bins
     return int(n_events * (26 + 36 + 4) + 2 * quad + hist + 8 * n0 * n1 * n2)
 
 

@@ -77,10 +77,12 @@ class OSEMServer:
                 xs = torch.zeros((max_events, 3), dtype=torch.float32, device="cuda")
                 xs[:, 0] = 1.0
                 tb = torch.zeros(max_events, dtype=torch.int16, device="cuda")
+                opts = dict(osem.OSEM_PLAN_OPTS)
+                opts.update(self.plan_opts)
                 with torch.cuda.stream(self.streams[slot]):
                     self.plans[(slot, g.shape)] = ops.jp_plan_create_subsets(
                         xs, torch.zeros_like(xs), g, n_sub, tof_bin=tb, tof_bin_width=self.tof.bin_width,
-                        **self.plan_opts)
+                        **opts)
                 torch.cuda.synchronize()
                 del xs, tb
                 if self.use_graphs:
