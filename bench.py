@@ -307,45 +307,72 @@ def run_ours(args):
 
 
 def run_e2e(args, W, plan, g, tof, dev, ws):
-    """Same step through the public API, inputs from pinned host memory and
-    the loss + gradient images read back every step."""
+    """Same step through the public API with the inputs copied from pinned
+    host memory and the loss and gradient images read back, every step.
+    Two device buffer sets: step k+1's inputs are copied on a side stream
+    while step k computes (and step k's results are read back on it), so the
+    copies overlap the compute; the timed region holds all of them."""
     from paper_2212_12519_gb300 import ops
     from paper_2212_12519_gb300.autograd import JosephTOFLM, PoissonLogLik
-    host = {k: W[k].cpu().pin_memory() for k in ("xs", "xe", "tb", "w", "bframe", "x")}
-    dbuf = {k: torch.empty_like(W[k]) for k in host}
-    out_grad = torch.empty(W["x"].shape, dtype=torch.float32).pin_memory()
-    out_loss = torch.empty((), dtype=torch.float64).pin_memory()
+    keys = ("xs", "xe", "tb", "w", "bframe", "x")
+    host = {k: W[k].cpu().pin_memory() for k in keys}
+    dbuf = [{k: torch.empty_like(W[k]) for k in keys} for _ in range(2)]
+    out_grad = [torch.empty(W["x"].shape, dtype=torch.float32).pin_memory() for _ in range(2)]
+    out_loss = [torch.empty((), dtype=torch.float64).pin_memory() for _ in range(2)]
     h2d = sum(v.numel() * v.element_size() for v in host.values())
-    d2h = out_grad.numel() * 4 + 8
-    stream = torch.cuda.current_stream()
+    d2h = out_grad[0].numel() * 4 + 8
+    comp = torch.cuda.current_stream()
+    copy = torch.cuda.Stream()
+    copied = [torch.cuda.Event() for _ in range(2)]
+    done = [torch.cuda.Event() for _ in range(2)]
+    results = [None, None]
 
-    def step():
-        for k in host:
-            dbuf[k].copy_(host[k], non_blocking=True)
-        ops.jp_plan_rebind(plan, dbuf["xs"], dbuf["xe"], W["offsets"], tof_bin=dbuf["tb"])
-        x = dbuf["x"].requires_grad_(True)
+    def h2d_into(b):
+        with torch.cuda.stream(copy):
+            copy.wait_event(done[b])  # buffer set b is free once its last step finished
+            for k in keys:
+                dbuf[b][k].copy_(host[k], non_blocking=True)
+            copied[b].record(copy)
+
+    def compute(b):
+        comp.wait_event(copied[b])
+        d = dbuf[b]
+        ops.jp_plan_rebind(plan, d["xs"], d["xe"], W["offsets"], tof_bin=d["tb"])
+        x = d["x"].detach().requires_grad_(True)
         p = JosephTOFLM.apply(x, plan, tof)
-        loss = PoissonLogLik.apply(p, plan, dbuf["w"], dbuf["bframe"])
+        loss = PoissonLogLik.apply(p, plan, d["w"], d["bframe"])
         loss.backward()
-        out_grad.copy_(x.grad, non_blocking=True)
-        out_loss.copy_(loss.detach(), non_blocking=True)
-        x.grad = None
-        dbuf["x"] = dbuf["x"].detach()
+        results[b] = (x.grad, loss.detach())
+        done[b].record(comp)
+        with torch.cuda.stream(copy):
+            copy.wait_event(done[b])
+            out_grad[b].copy_(results[b][0], non_blocking=True)
+            out_loss[b].copy_(results[b][1], non_blocking=True)
 
-    for _ in range(max(1, min(args.warmup, 2))):
-        step()
+    def run(nsteps):
+        h2d_into(0)
+        for k in range(nsteps):
+            b = k % 2
+            if k + 1 < nsteps:
+                h2d_into(1 - b)
+            compute(b)
+        comp.wait_stream(copy)
+
+    for e in done:
+        e.record(comp)
+    run(max(1, min(args.warmup, 2)))
     torch.cuda.synchronize()
     n = max(2, args.steps // 2)
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    for _ in range(n):
-        step()
-    t1.record(stream)
+    t0.record(comp)
+    run(n)
+    t1.record(comp)
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1) / n
     return {"value": W["xs"].shape[0] * ws / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
-            "steps": n, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+            "steps": n, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "copies": "pinned host <-> device every step, overlapped with compute (2 buffer sets)"}
 
 
 # ---------------------------------------------------------------------------

@@ -277,3 +277,44 @@ def test_osem_elementwise(ops):
     np.testing.assert_allclose(dx.cpu().numpy(), ref, rtol=2e-6)
     v = rng.uniform(0, 1, size=1_000_001).astype(np.float32)
     assert float(ops.jp_sum_f64(cuda(v))) == pytest.approx(float(v.astype(np.float64).sum()), rel=1e-12)
+
+
+@pytest.mark.parametrize("shape", [(1, 24, 20), (17, 1, 9), (11, 13, 1), (1, 1, 30)])
+def test_degenerate_axes(ops, shape):
+    """Images with a single voxel along one or two axes (2D and 1D grids),
+    every mode, planned and planless."""
+    g = synth.ImageGeom.centred(shape, (2.0, 1.5, 2.5))
+    rng = np.random.Generator(np.random.PCG64(6101))
+    img = rng.uniform(0, 2, size=shape).astype(np.float32)
+    xs, xe = synth.random_lors(5000, g, seed=6102)
+    tof = synth.TofParams(bin_width=6.0, sigma=5.0, n_sigmas=3.0, n_bins=9)
+    tb = rng.integers(-4, 5, size=len(xs)).astype(np.int16)
+    for mode in ["nontof", "tof_sino", "tof_lm"]:
+        t = None if mode == "nontof" else tof
+        kw = dict(tof_bin=tb) if mode == "tof_lm" else {}
+        p_or, amb = oracle.fwd(xs, xe, img, g, mode, t, amb_eps=AMB_EPS, return_amb=True, **kw)
+        plan = ops.jp_plan_create(cuda(xs), cuda(xe), g, tof_bin=cuda(tb), tof_bin_width=tof.bin_width)
+        if mode == "nontof":
+            p = ops.jp_fwd(plan, cuda(img))
+        elif mode == "tof_sino":
+            p = ops.jp_fwd_tof_sino(plan, cuda(img), tof)
+        else:
+            p = ops.jp_fwd_tof_lm(plan, cuda(img), tof)
+        q = ops.jp_fwd_lors(cuda(xs), cuda(xe), cuda(img), g, mode, t, tof_bin=cuda(tb) if mode == "tof_lm" else None)
+        torch.cuda.synchronize()
+        assert fwd_err(p.cpu().numpy(), p_or, amb) <= FWD_TOL, mode
+        assert fwd_err(q.cpu().numpy(), p_or, amb) <= FWD_TOL, mode
+        nout = tof.n_bins if mode == "tof_sino" else 1
+        y = rng.uniform(0, 1, size=len(xs) * nout).astype(np.float32)
+        b_or = oracle.back(xs, xe, y, g, mode, t, **kw)
+        out = torch.zeros(shape, device="cuda")
+        dy = cuda(y.reshape(len(xs), nout) if mode == "tof_sino" else y)
+        if mode == "nontof":
+            ops.jp_back(plan, dy, out)
+        elif mode == "tof_sino":
+            ops.jp_back_tof_sino(plan, dy, tof, out)
+        else:
+            ops.jp_back_tof_lm(plan, dy, tof, out)
+        torch.cuda.synchronize()
+        if np.abs(b_or).max() > 0:
+            assert rel_l2(out.cpu().numpy(), b_or) <= BACK_TOL, mode
