@@ -95,14 +95,18 @@ typedef struct {
   float tof_bin_width;    /* mm; > 0 with tof_bin given: bin listmode events by
                              their TOF window centre; 0 = ignore */
   int32_t lors_per_warp;  /* LORs a warp walks at once: 32 = one LOR per thread;
-                             1, 2 or 4 = 32, 16 or 8 lanes step through consecutive
-                             planes of one LOR (coalesced); 0 = per-mode default */
+                             1, 2, 4, 8 or 16 = 32, 16, 8, 4 or 2 lanes step through
+                             consecutive planes of one LOR (coalesced); 0 = per-mode
+                             default */
   int32_t flags;          /* JP_PLAN_KEEP_ORDER: no sorting (identity order);
                              JP_PLAN_TOF_EXACT: evaluate every TOF weight with erff
                              instead of the interpolated table (see below) */
   int32_t zoff_bins;      /* bins over the offset along axis c (the fastest image
                              axis for principal axes 0 and 1) at the central plane,
                              the last (fastest) key field (0 = 8; 1 = not binned) */
+  int32_t max_ctas_per_sm;/* cap on the resident CTAs per SM of the persistent
+                             projection kernels, leaving room for work on other
+                             streams (0 = as many as fit) */
 } jp_plan_opts;
 
 #define JP_PLAN_KEEP_ORDER 1
@@ -284,8 +288,9 @@ uint64_t jp_launch_count(void);
  * projections).
  * Its scratch is a workspace compiled into the library: 2^20 entries of 16
  * bytes (16 MiB), held by every GPU that loads the library until the process
- * exits.  The image must fit it: sum over a of n_a (n_b + 2)(n_c + 2) <= 2^20
- * (for instance 64 x 64 x 16, or about 70^3), else JP_ERR_ARG.  The first
+ * exits.  The image must fit it: sum over a of n_a' (n_b + 2)(n_c + 2) <= 2^20
+ * with n_a' = n_a rounded up to even (for instance 64 x 64 x 16, or about
+ * 70^3), else JP_ERR_ARG.  The first
  * call on a device looks the workspace address up (cudaGetSymbolAddress),
  * so make that first call before any stream capture.  Every call shares the
  * one workspace (it is cleared at the start of each call): calls that

@@ -239,7 +239,7 @@ __device__ __forceinline__ float tof_g(float dist, const DevTof& t) {
 //   plane-major   index = (k * nb2 + (i + 1)) * nc2 + (j + 1): the lanes of a
 //                 warp following 32 neighbouring LORs (one per thread) read
 //                 nearby entries of the same plane rows;
-//   plane-fastest index = ((i + 1) * nc2 + (j + 1)) * n_a + k: the lanes of a
+//   plane-fastest index = ((i + 1) * nc2 + (j + 1)) * nap + k: the lanes of a
 //                 group walking consecutive planes of one LOR touch
 //                 consecutive 16-byte entries (coalesced reductions).
 // ---------------------------------------------------------------------------
@@ -249,7 +249,9 @@ __device__ __forceinline__ int quad_index(bool kfast, int k, int ip, int jp, int
 
 struct QuadLayout {
   int nb2[3], nc2[3];  // n_b + 2, n_c + 2 for axis a
-  int64_t size[3];     // n_a * nb2 * nc2 entries of Q_a
+  int nap[3];          // n_a rounded up to even: in plane-fastest order the two
+                       // entries of a 32-byte sector are always planes 2m, 2m+1
+  int64_t size[3];     // nap * nb2 * nc2 entries of Q_a
   int64_t base[3];     // float4 offset of Q_a inside one slot
   int64_t slot;        // float4 per slot (one image)
 };
@@ -261,7 +263,8 @@ inline QuadLayout quad_layout(const jp_image_geom& g) {
     int b = (a == 0) ? 1 : 0, c = (a == 2) ? 1 : 2;
     q.nb2[a] = g.n[b] + 2;
     q.nc2[a] = g.n[c] + 2;
-    q.size[a] = (int64_t)g.n[a] * q.nb2[a] * q.nc2[a];
+    q.nap[a] = g.n[a] + (g.n[a] & 1);
+    q.size[a] = (int64_t)q.nap[a] * q.nb2[a] * q.nc2[a];
     q.base[a] = off;
     off += q.size[a];
   }

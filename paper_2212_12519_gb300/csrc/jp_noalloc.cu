@@ -142,7 +142,7 @@ extern "C" int jp_back_tof_lm_noalloc(const float* xs, const float* xe, const in
   if (rc) return rc;
   p.ql = quad_layout(*g);
   if (p.ql.slot > kNoAllocQuads)
-    return fail(JP_ERR_ARG, "image too large for the fixed workspace: sum_a n_a (n_b+2)(n_c+2) must be <= 2^20");
+    return fail(JP_ERR_ARG, "image too large for the fixed workspace: sum_a n_a' (n_b+2)(n_c+2) must be <= 2^20");
   float4* q = nullptr;
   rc = workspace(&q);
   if (rc) return rc;

@@ -393,8 +393,8 @@ extern "C" int jp_plan_create_batch(jp_plan* out, const float* xs, const float* 
   if (o.slope_bins < 1 || o.offset_bins < 1 || o.window_bins < 1 || o.zoff_bins < 1)
     return fail(JP_ERR_ARG, "bin counts must be >= 1");
   if (o.lors_per_warp != 0 && o.lors_per_warp != 1 && o.lors_per_warp != 2 && o.lors_per_warp != 4 &&
-      o.lors_per_warp != 32)
-    return fail(JP_ERR_ARG, "opts.lors_per_warp must be 0, 1, 2, 4 or 32");
+      o.lors_per_warp != 8 && o.lors_per_warp != 16 && o.lors_per_warp != 32)
+    return fail(JP_ERR_ARG, "opts.lors_per_warp must be 0, 1, 2, 4, 8, 16 or 32");
   if (!(o.tof_bin_width >= 0.f) || !isfinite(o.tof_bin_width)) return fail(JP_ERR_ARG, "opts.tof_bin_width must be finite and >= 0");
   int window_bins = (o.tof_bin_width > 0.f && tof_bin) ? o.window_bins : 1;
   int64_t kpf = 3LL * o.slope_bins * o.offset_bins * window_bins * o.zoff_bins;

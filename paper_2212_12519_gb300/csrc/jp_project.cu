@@ -101,6 +101,7 @@ struct ProjParams {
   const float* sens;  // sensitivity image
   float sens_scale;
   int perm_in_rec;    // caller index in the first record's .w (no TOF centre offsets)
+  int max_per_sm;     // host side: cap on resident CTAs per SM for persistent launches (0 = occupancy)
   // persistent kernels take chunks of LORs from this counter (reset by the
   // workspace kernel launched just before them), so the chunks in flight
   // stay a contiguous window of the binned order (one frame's image at a time)
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(kMaxBlock) planned_kernel(const ProjParams p) 
     const int a = r.a;
     const int nc2 = sel3(a, p.ql.nc2[0], p.ql.nc2[1], p.ql.nc2[2]);
     const int nb2 = sel3(a, p.ql.nb2[0], p.ql.nb2[1], p.ql.nb2[2]);
-    const int na = sel3(a, p.g.n[0], p.g.n[1], p.g.n[2]);
+    const int na = sel3(a, p.ql.nap[0], p.ql.nap[1], p.ql.nap[2]);  // k-stride of plane-fastest quads
     const int64_t qoff = (int64_t)slot * p.ql.slot + sel3(a, p.ql.base[0], p.ql.base[1], p.ql.base[2]);
     const float ub = (float)r.nb, wb = (float)r.nc;
 
@@ -415,6 +416,7 @@ __global__ void __launch_bounds__(kMaxBlock) group_kernel(const ProjParams p) {
         ddl = __shfl_sync(0xffffffffu, delta, src);
       }
       const int na = sel3(a, p.g.n[0], p.g.n[1], p.g.n[2]);
+      const int nap = sel3(a, p.ql.nap[0], p.ql.nap[1], p.ql.nap[2]);
       const int nb = (a == 0) ? p.g.n[1] : p.g.n[0];
       const int nc = (a == 2) ? p.g.n[1] : p.g.n[2];
       const int nc2 = nc + 2;
@@ -430,7 +432,7 @@ __global__ void __launch_bounds__(kMaxBlock) group_kernel(const ProjParams p) {
           const float w = fminf(fmaxf(fmaf(kk, dw, wc), -1.f), wb);
           const float fu = floorf(u), fw = floorf(w);
           const float al = u - fu, be = w - fw;
-          const float4 v = __ldg(Qa + (((int)fu + 1) * nc2 + ((int)fw + 1)) * na + k);
+          const float4 v = __ldg(Qa + (((int)fu + 1) * nc2 + ((int)fw + 1)) * nap + k);
           const float top = fmaf(be, v.z - v.x, v.x);
           const float bot = fmaf(be, v.w - v.y, v.y);
           const float s = fmaf(al, bot - top, top);
@@ -438,13 +440,16 @@ __global__ void __launch_bounds__(kMaxBlock) group_kernel(const ProjParams p) {
           else sum = fmaf(tof_weight<LUT>(lut, fmaf(kk, ddt, dd0), T, inv_h), s, sum);
         }
       }
-      for (int k = k0 + gl; BACK && k <= k1; k += G) {
+      // start the group on an even plane: neighbouring lanes then cover the
+      // (2m, 2m+1) plane pairs that share a 32-byte sector
+      for (int k = (k0 & ~1) + gl; BACK && k <= k1; k += G) {
+        if (k < k0) continue;
         const float kk = (float)k - kc;
         const float u = fminf(fmaxf(fmaf(kk, du, uc), -1.f), ub);
         const float w = fminf(fmaxf(fmaf(kk, dw, wc), -1.f), wb);
         const float fu = floorf(u), fw = floorf(w);
         const float al = u - fu, be = w - fw;
-        const int q = (((int)fu + 1) * nc2 + ((int)fw + 1)) * na + k;
+        const int q = (((int)fu + 1) * nc2 + ((int)fw + 1)) * nap + k;
         {
           float coef = w0;
           if (MODE == 2) coef *= tof_weight<LUT>(lut, fmaf(kk, ddt, dd0), T, inv_h);
@@ -546,6 +551,7 @@ __global__ void __launch_bounds__(kMaxBlock) osem_kernel(const ProjParams p) {
       const float dd0 = __shfl_sync(0xffffffffu, d0, src);
       const float ddt = __shfl_sync(0xffffffffu, r.dt, src);
       const int na = sel3(a, p.g.n[0], p.g.n[1], p.g.n[2]);
+      const int nap = sel3(a, p.ql.nap[0], p.ql.nap[1], p.ql.nap[2]);
       const int nb = (a == 0) ? p.g.n[1] : p.g.n[0];
       const int nc = (a == 2) ? p.g.n[1] : p.g.n[2];
       const int nc2 = nc + 2;
@@ -560,7 +566,7 @@ __global__ void __launch_bounds__(kMaxBlock) osem_kernel(const ProjParams p) {
         const float w = fminf(fmaxf(fmaf(kk, dw, wc), -1.f), wb);
         const float fu = floorf(u), fw = floorf(w);
         const float al = u - fu, be = w - fw;
-        const float4 v = __ldg(p.quads + qoff + (((int)fu + 1) * nc2 + ((int)fw + 1)) * na + k);
+        const float4 v = __ldg(p.quads + qoff + (((int)fu + 1) * nc2 + ((int)fw + 1)) * nap + k);
         const float top = fmaf(be, v.z - v.x, v.x);
         const float bot = fmaf(be, v.w - v.y, v.y);
         sum = fmaf(tof_weight<LUT>(lut, fmaf(kk, ddt, dd0), T, inv_h), fmaf(al, bot - top, top), sum);
@@ -568,7 +574,8 @@ __global__ void __launch_bounds__(kMaxBlock) osem_kernel(const ProjParams p) {
       sum = group_sum<G>(sum);
       // ratio and back projection of it
       const float coef0 = (k0 <= k1) ? w0 / fmaf(w0, sum, bg) : 0.f;
-      for (int k = k0 + gl; k <= k1 && coef0 != 0.f; k += G) {
+      for (int k = (k0 & ~1) + gl; k <= k1 && coef0 != 0.f; k += G) {
+        if (k < k0) continue;
         const float kk = (float)k - kc;
         const float u = fminf(fmaxf(fmaf(kk, du, uc), -1.f), ub);
         const float w = fminf(fmaxf(fmaf(kk, dw, wc), -1.f), wb);
@@ -576,7 +583,7 @@ __global__ void __launch_bounds__(kMaxBlock) osem_kernel(const ProjParams p) {
         const float al = u - fu, be = w - fw;
         const float coef = coef0 * tof_weight<LUT>(lut, fmaf(kk, ddt, dd0), T, inv_h);
         const float ca = (1.f - al) * coef, cb = al * coef;
-        atomicAdd(p.quads_bp + qoff + (((int)fu + 1) * nc2 + ((int)fw + 1)) * na + k,
+        atomicAdd(p.quads_bp + qoff + (((int)fu + 1) * nc2 + ((int)fw + 1)) * nap + k,
                   make_float4(ca * (1.f - be), cb * (1.f - be), ca * be, cb * be));
       }
     }
@@ -603,7 +610,7 @@ __global__ void osem_update_kernel(const ProjParams p, float* __restrict__ x) {
       const int I = (a == 0) ? i1 : i0;
       const int J = (a == 2) ? i1 : i2;
       const int nc2 = p.ql.nc2[a], nb2 = p.ql.nb2[a];
-      const int na = g.n[a];
+      const int na = p.ql.nap[a];
       const float4* Q = p.quads_bp + p.ql.base[a];
       bp += Q[quad_index(true, k, I + 1, J + 1, na, nb2, nc2)].x + Q[quad_index(true, k, I, J + 1, na, nb2, nc2)].y +
             Q[quad_index(true, k, I + 1, J, na, nb2, nc2)].z + Q[quad_index(true, k, I, J, na, nb2, nc2)].w;
@@ -636,8 +643,9 @@ __global__ void quad_build_kernel(const ProjParams p) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     int k, i, jj;
     if (p.kfast) {
-      const int t = (int)(e / na);
-      k = (int)(e - (int64_t)t * na);
+      const int nap = sel3(a, p.ql.nap[0], p.ql.nap[1], p.ql.nap[2]);
+      const int t = (int)(e / nap);
+      k = (int)(e - (int64_t)t * nap);
       i = t / nc2 - 1;
       jj = t - (t / nc2) * nc2 - 1;
     } else {
@@ -645,6 +653,10 @@ __global__ void quad_build_kernel(const ProjParams p) {
       jj = (int)(e - (int64_t)t * nc2) - 1;
       k = t / nb2;
       i = t - k * nb2 - 1;
+    }
+    if (k >= na) {  // padding plane of an odd plane count
+      Q[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+      continue;
     }
     const bool i0 = (unsigned)i < (unsigned)nb, i1 = (unsigned)(i + 1) < (unsigned)nb;
     const bool j0 = (unsigned)jj < (unsigned)nc, j1 = (unsigned)(jj + 1) < (unsigned)nc;
@@ -691,7 +703,7 @@ __global__ void quad_reduce_kernel(const ProjParams p) {
       const int I = (a == 0) ? i1 : i0;                 // index along b
       const int J = (a == 2) ? i1 : i2;                 // index along c
       const int nc2 = p.ql.nc2[a], nb2 = p.ql.nb2[a];
-      const int na = g.n[a];
+      const int na = p.ql.nap[a];
       const float4* Q = Qs + p.ql.base[a];
       const bool kf = p.kfast;
       // padded positions: voxel I sits at I + 1
@@ -849,6 +861,7 @@ int launch_planned(const ProjParams& p, int block, cudaStream_t st) {
   if (rc) return rc;
   int per_sm = 0;
   JP_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem));
+  if (p.max_per_sm > 0 && per_sm > p.max_per_sm) per_sm = p.max_per_sm;
   if (per_sm < 1) per_sm = 1;
   int64_t need = (p.n + block - 1) / block;
   int64_t grid = (int64_t)sm_count() * per_sm;
@@ -866,6 +879,7 @@ int launch_group(const ProjParams& p, int block, cudaStream_t st) {
   const size_t smem = (MODE != 0 && LUT) ? kLut * sizeof(float2) : 0;
   int per_sm = 0;
   JP_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem));
+  if (p.max_per_sm > 0 && per_sm > p.max_per_sm) per_sm = p.max_per_sm;
   if (per_sm < 1) per_sm = 1;
   int64_t need = (p.n + block - 1) / block;
   int64_t grid = (int64_t)sm_count() * per_sm;
@@ -883,6 +897,8 @@ int launch_group_lpw(const ProjParams& p, int block, int lpw, cudaStream_t st) {
     case 1: return launch_group<MODE, BACK, LUT, 32>(p, block, st);
     case 2: return launch_group<MODE, BACK, LUT, 16>(p, block, st);
     case 4: return launch_group<MODE, BACK, LUT, 8>(p, block, st);
+    case 8: return launch_group<MODE, BACK, LUT, 4>(p, block, st);
+    case 16: return launch_group<MODE, BACK, LUT, 2>(p, block, st);
     default: return launch_planned<MODE, BACK, LUT>(p, block, st);
   }
 }
@@ -954,6 +970,7 @@ int planned(jp_plan pl, int mode, bool back, const float* in, float* out, int64_
   p.shared = (img_stride == 0 || pl->n_frames == 1) ? 1 : 0;
   p.counter = pl->work_counter;
   p.perm_in_rec = pl->has_delta ? 0 : 1;
+  p.max_per_sm = pl->opts.max_ctas_per_sm;
   if (back) { p.proj_in = in; p.img_out = out; } else { p.img_in = in; p.proj_out = out; }
   const int slots = p.shared ? 1 : pl->n_frames;
   if (slots * 3 > 65535) return fail(JP_ERR_ARG, "too many frames with distinct images (max 21845)");

@@ -44,7 +44,8 @@ class TofC(ctypes.Structure):
 
 class PlanOptsC(ctypes.Structure):
     _fields_ = [("block", I32), ("slope_bins", I32), ("offset_bins", I32), ("window_bins", I32),
-                ("tof_bin_width", F32), ("lors_per_warp", I32), ("flags", I32), ("zoff_bins", I32)]
+                ("tof_bin_width", F32), ("lors_per_warp", I32), ("flags", I32), ("zoff_bins", I32),
+                ("max_ctas_per_sm", I32)]
 
 
 _lib = None
@@ -188,11 +189,11 @@ class Plan:
 
 
 def _opts(block=0, slope_bins=0, offset_bins=0, window_bins=0, tof_bin_width=0.0, keep_order=False,
-          tof_exact=False, lors_per_warp=0, interleaved=False, zoff_bins=0):
+          tof_exact=False, lors_per_warp=0, interleaved=False, zoff_bins=0, max_ctas_per_sm=0):
     flags = ((JP_PLAN_KEEP_ORDER if keep_order else 0) | (JP_PLAN_TOF_EXACT if tof_exact else 0)
              | (JP_PLAN_INTERLEAVED if interleaved else 0))
     return PlanOptsC(int(block), int(slope_bins), int(offset_bins), int(window_bins),
-                     float(tof_bin_width), int(lors_per_warp), flags, int(zoff_bins))
+                     float(tof_bin_width), int(lors_per_warp), flags, int(zoff_bins), int(max_ctas_per_sm))
 
 
 def jp_plan_create_batch(xs, xe, geom, frame_offsets, tof_bin=None, delta=None, stream=None,
