@@ -119,6 +119,7 @@ def measured_peaks():
 # workload
 # ---------------------------------------------------------------------------
 def make_tof_lm_batch(rank: int, n_frames: int, events: int, device):
+    """8 phantoms x ``events`` TOF listmode events each (seeded per frame and rank)."""
     from paper_2212_12519_gb300 import synth
     g = synth.GEOM_CLINICAL
     tof = synth.TOF_CLINICAL
@@ -153,7 +154,7 @@ def make_tof_lm_batch(rank: int, n_frames: int, events: int, device):
 def run_ours(args):
     import torch.distributed as dist
     from paper_2212_12519_gb300 import ops
-    from paper_2212_12519_gb300.autograd import JosephTOFLM, PoissonLogLik
+    from paper_2212_12519_gb300.autograd import JosephNonTOF, JosephTOFLM, PoissonLogLik
     from paper_2212_12519_gb300 import build as jbuild
 
     ws, rank, local = dist_env()
@@ -164,15 +165,28 @@ def run_ours(args):
     jbuild.build()
     ops.load()
     n_frames, epf = args.frames, args.events
+    nontof = args.workload == "nontof_lm"
     W = make_tof_lm_batch(rank, n_frames, epf, dev)
     g, tof = W["geom"], W["tof"]
     n_total = W["xs"].shape[0]
+    if nontof:
+        # same events without their TOF bins
+        W["tb"] = None
     opts = {}
     if not args.no_autotune:
         from paper_2212_12519_gb300 import autotune
-        opts = autotune.tune(W["xs"][:epf], W["xe"][:epf], g, mode="tof_lm", tof=tof, tof_bin=W["tb"][:epf])
+        if args.workload == "nontof_lm":
+            opts = autotune.tune(W["xs"][:epf], W["xe"][:epf], g, mode="nontof")
+        else:
+            opts = autotune.tune(W["xs"][:epf], W["xe"][:epf], g, mode="tof_lm", tof=tof, tof_bin=W["tb"][:epf])
     plan = ops.jp_plan_create_batch(W["xs"], W["xe"], g, W["offsets"], tof_bin=W["tb"],
-                                    tof_bin_width=tof.bin_width, **opts)
+                                    tof_bin_width=0.0 if nontof else tof.bin_width, **opts)
+    if nontof:
+        # background: 10 % of each frame's mean non-TOF projection
+        p0 = ops.jp_fwd(plan, W["x"]).view(n_frames, epf).double().mean(dim=1)
+        W["bvals"] = [float(0.1 * v) for v in p0.cpu()]
+        W["bframe"] = torch.tensor(W["bvals"], dtype=torch.float32, device=dev)
+        del p0
     x = W["x"].clone().requires_grad_(True)
     stream = torch.cuda.current_stream()
 
@@ -191,12 +205,17 @@ def run_ours(args):
         @staticmethod
         def forward(ctx, xx):
             ctx.shape = xx.shape
+            if nontof:
+                return timed("fwd", lambda: ops.jp_fwd(plan, xx.contiguous()))
             return timed("fwd", lambda: ops.jp_fwd_tof_lm(plan, xx.contiguous(), tof))
 
         @staticmethod
         def backward(ctx, gp):
             gx = torch.zeros(ctx.shape, dtype=torch.float32, device=gp.device)
-            timed("back", lambda: ops.jp_back_tof_lm(plan, gp.contiguous(), tof, gx))
+            if nontof:
+                timed("back", lambda: ops.jp_back(plan, gp.contiguous(), gx))
+            else:
+                timed("back", lambda: ops.jp_back_tof_lm(plan, gp.contiguous(), tof, gx))
             return gx
 
     def step(record=True):
@@ -205,7 +224,10 @@ def run_ours(args):
         else:
             ops.jp_plan_rebind(plan, W["xs"], W["xe"], W["offsets"], tof_bin=W["tb"])
         x.grad = None
-        p = TimedTOFLM.apply(x) if record else JosephTOFLM.apply(x, plan, tof)
+        if record:
+            p = TimedTOFLM.apply(x)
+        else:
+            p = JosephNonTOF.apply(x, plan) if nontof else JosephTOFLM.apply(x, plan, tof)
         loss = PoissonLogLik.apply(p, plan, W["w"], W["bframe"])
         loss.backward()
         return loss
@@ -242,23 +264,24 @@ def run_ours(args):
     kern = {k: statistics.mean(s.elapsed_time(e) for s, e in v) for k, v in timers.items() if v}
 
     # exact algorithmic work of one TOF-LM launch
-    samples = ops.jp_count_samples(plan, "tof_lm", tof)
+    samples = ops.jp_count_samples(plan, "nontof" if nontof else "tof_lm", tof)
     value = n_total * ws / (ms / 1e3)
 
     # ---- e2e through the public API with host buffers --------------------
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(args, W, plan, g, tof, dev, ws)
+        e2e = run_e2e(args, W, plan, g, tof, dev, ws, nontof)
     # L2 reduction ceiling (one 16-byte RED per plane sample bounds the back projection)
     red = {pt: ops.jp_bench_red(pattern=pt) for pt in (0, 1, 2)}
     cpu_sample = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu_sample = _oracle_events(W, min(W["xs"].shape[0], 8_000_000))
     plan.destroy()
-    del W["xs"], W["xe"], W["tb"], W["w"], W["bvec"]
+    del W["xs"], W["xe"], W["w"], W["bvec"]
+    W["tb"] = None
     torch.cuda.empty_cache()
     serving = None
-    if not args.no_serving and rank == 0:
+    if not args.no_serving and rank == 0 and not nontof:
         rates = [float(r) for r in args.serving_rates.split(",")]
         serving = run_serving(n_requests=args.serving_requests, rates=rates, max_slots=args.serving_slots)
 
@@ -267,28 +290,32 @@ def run_ours(args):
         # dominant kernel: the back projection (scatter), reported against HBM
         dom = "back" if kern.get("back", 0) >= kern.get("fwd", 0) else "fwd"
         nvox = int(np.prod(g.shape))
-        alg_bytes = n_total * (24 + 2 + 4) + n_frames * nvox * 4 * (2 if dom == "back" else 1)
+        alg_bytes = n_total * (24 + (0 if nontof else 2) + 4) + n_frames * nvox * 4 * (2 if dom == "back" else 1)
         achieved = alg_bytes / (kern[dom] / 1e3) / 1e9
         # binding resource: L2 reduction sectors of the back projection vs the measured ceiling
         red_rate = samples / (kern["back"] / 1e3)
         sec_rate = red_rate * BACK_SECTORS_PER_SAMPLE
         sec_peak = max(r["sectors_per_s"] for r in red.values())
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "metric": METRIC if not nontof else "non-TOF listmode fwd+back events/s",
+            "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"tof_lm_batch{n_frames}x{epf // 1_000_000}M_200x200x71",
+            "config": {"workload": f"{'nontof' if nontof else 'tof'}_lm_batch{n_frames}x{epf // 1_000_000}M_200x200x71",
                        "frames_per_gpu": n_frames, "events_per_frame": epf, "image": list(g.shape),
-                       "tof_bins": tof.n_bins, "l2": "inputs (>10 GB/step) larger than L2, no flush",
+                       "tof_bins": 0 if nontof else tof.n_bins,
+                       "l2": "inputs (>10 GB/step) larger than L2, no flush",
                        "parallelism": f"dp{ws} (independent batches)", "plan_opts": opts},
             "kernel_ms": kern,
             "samples_per_step": samples,
             "events_per_s_excl_binning": n_total * ws / ((ms - kern.get("bin", 0.0)) / 1e3),
-            "roofline": {"bound": "hbm", "kernel": f"{dom}_tof_lm", "achieved": achieved,
+            "roofline": {"bound": "hbm", "kernel": f"{dom}_{'nontof' if nontof else 'tof'}_lm", "achieved": achieved,
                          "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                         "traffic": (BACK_DRAM_BYTES_PER_EVENT * n_total if dom == "back" else None),
+                         "traffic": (BACK_DRAM_BYTES_PER_EVENT * n_total if dom == "back" and not nontof
+                                     else None),
                          "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes},
-            "binding_roofline": {"kernel": "back_tof_lm", "resource": "L2 reduction sectors (16-byte RED per sample)",
+            "binding_roofline": {"kernel": "back_nontof_lm" if nontof else "back_tof_lm",
+                                 "resource": "L2 reduction sectors (16-byte RED per sample)",
                                  "achieved": sec_rate, "peak": sec_peak, "unit": "sectors/s",
                                  "frac": sec_rate / sec_peak, "reductions_per_s": red_rate,
                                  "sectors_per_reduction": BACK_SECTORS_PER_SAMPLE,
@@ -300,21 +327,22 @@ def run_ours(args):
             "serving": serving,
         }
         if cpu_sample is not None:
-            line["cpu_baseline"] = cpu_baseline(cpu_sample, W["bvals"][0], g, tof, n_total, target_s=args.cpu_seconds)
+            line["cpu_baseline"] = cpu_baseline(cpu_sample, W["bvals"][0], g, None if nontof else tof, n_total,
+                                                target_s=args.cpu_seconds)
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
 
 
-def run_e2e(args, W, plan, g, tof, dev, ws):
+def run_e2e(args, W, plan, g, tof, dev, ws, nontof=False):
     """Same step through the public API with the inputs copied from pinned
     host memory and the loss and gradient images read back, every step.
     Two device buffer sets: step k+1's inputs are copied on a side stream
     while step k computes (and step k's results are read back on it), so the
     copies overlap the compute; the timed region holds all of them."""
     from paper_2212_12519_gb300 import ops
-    from paper_2212_12519_gb300.autograd import JosephTOFLM, PoissonLogLik
-    keys = ("xs", "xe", "tb", "w", "bframe", "x")
+    from paper_2212_12519_gb300.autograd import JosephNonTOF, JosephTOFLM, PoissonLogLik
+    keys = ("xs", "xe", "w", "bframe", "x") if nontof else ("xs", "xe", "tb", "w", "bframe", "x")
     host = {k: W[k].cpu().pin_memory() for k in keys}
     dbuf = [{k: torch.empty_like(W[k]) for k in keys} for _ in range(2)]
     out_grad = [torch.empty(W["x"].shape, dtype=torch.float32).pin_memory() for _ in range(2)]
@@ -337,9 +365,9 @@ def run_e2e(args, W, plan, g, tof, dev, ws):
     def compute(b):
         comp.wait_event(copied[b])
         d = dbuf[b]
-        ops.jp_plan_rebind(plan, d["xs"], d["xe"], W["offsets"], tof_bin=d["tb"])
+        ops.jp_plan_rebind(plan, d["xs"], d["xe"], W["offsets"], tof_bin=d.get("tb"))
         x = d["x"].detach().requires_grad_(True)
-        p = JosephTOFLM.apply(x, plan, tof)
+        p = JosephNonTOF.apply(x, plan) if nontof else JosephTOFLM.apply(x, plan, tof)
         loss = PoissonLogLik.apply(p, plan, d["w"], d["bframe"])
         loss.backward()
         results[b] = (x.grad, loss.detach())
@@ -590,17 +618,19 @@ def run_serving(n_requests=200, rates=(1.0,), pool_events=20_000_000, max_slots=
 def _oracle_events(W, n):
     xs = W["xs"][:n].cpu().numpy()
     xe = W["xe"][:n].cpu().numpy()
-    tb = W["tb"][:n].cpu().numpy()
+    tb = W["tb"][:n].cpu().numpy() if W["tb"] is not None else None
     img = W["x"][0].detach().cpu().numpy()
     w = W["w"][:n].cpu().numpy()
     return xs, xe, tb, img, w
 
 
 def oracle_step(xs, xe, tb, img, w, g, tof, b, threads):
+    """FP64 oracle fwd + ratio + back of one event sample (non-TOF when tof is None)."""
     import oracle
-    p = oracle.fwd(xs, xe, img, g, "tof_lm", tof, tof_bin=tb, threads=threads)
+    mode = "nontof" if tof is None else "tof_lm"
+    p = oracle.fwd(xs, xe, img, g, mode, tof, tof_bin=tb, threads=threads)
     q = w / (p + b)
-    oracle.back(xs, xe, q, g, "tof_lm", tof, tof_bin=tb, threads=threads)
+    oracle.back(xs, xe, q, g, mode, tof, tof_bin=tb, threads=threads)
 
 
 def cpu_baseline(sample, b, g, tof, n_total, target_s=12.0):
@@ -612,11 +642,11 @@ def cpu_baseline(sample, b, g, tof, n_total, target_s=12.0):
     xs, xe, tb, img, w = sample
     n0 = min(100_000, len(xs))
     t = time.perf_counter()
-    oracle_step(xs[:n0], xe[:n0], tb[:n0], img, w[:n0], g, tof, b, threads)
+    oracle_step(xs[:n0], xe[:n0], None if tb is None else tb[:n0], img, w[:n0], g, tof, b, threads)
     dt = time.perf_counter() - t
     n = int(min(len(xs), max(n0, n0 * target_s / max(dt, 1e-3))))
     t = time.perf_counter()
-    oracle_step(xs[:n], xe[:n], tb[:n], img, w[:n], g, tof, b, threads)
+    oracle_step(xs[:n], xe[:n], None if tb is None else tb[:n], img, w[:n], g, tof, b, threads)
     dt = time.perf_counter() - t
     return {"value": n / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"first {n} events of frame 0 (of {n_total} in the batch), FP64 fwd+back, {dt:.1f} s"}
@@ -639,7 +669,12 @@ def run_reference(args):
     import oracle
     oracle.build()
     threads = os.cpu_count() or 1
-    a = (xs.numpy(), xe.numpy(), tb.numpy(), ph.numpy(), w.numpy())
+    nontof = args.workload == "nontof_lm"
+    a = (xs.numpy(), xe.numpy(), None if nontof else tb.numpy(), ph.numpy(), w.numpy())
+    if nontof:
+        tof = None
+        m = min(n, 20_000)
+        b = 0.1 * float(oracle.fwd(a[0][:m], a[1][:m], a[3], g, "nontof", None, threads=threads).mean())
     for _ in range(args.warmup):
         oracle_step(*a, g, tof, b, threads)
     t = time.perf_counter()
@@ -647,11 +682,13 @@ def run_reference(args):
         oracle_step(*a, g, tof, b, threads)
     dt = (time.perf_counter() - t) / args.steps
     value = n / dt
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+    line = {"impl": "reference", "metric": "non-TOF listmode fwd+back events/s" if nontof else METRIC,
+            "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"tof_lm_batch{N_FRAMES}x{EVENTS_PER_FRAME // 1_000_000}M_200x200x71",
+            "config": {"workload": f"{'nontof' if nontof else 'tof'}_lm_batch{N_FRAMES}x"
+                                   f"{EVENTS_PER_FRAME // 1_000_000}M_200x200x71",
                        "sample": f"{n} events of frame 0 per step"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"{n} events per step, FP64 fwd+back"},
@@ -675,8 +712,8 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=200)
     ap.add_argument("--serving-rates", default="0.5,1.0,1.5")
     ap.add_argument("--workload", default="tof_lm",
-                    choices=["tof_lm", "sino_small", "sino_clinical", "tof_sino", "osem", "profile_case",
-                             "profile_osem"])
+                    choices=["tof_lm", "nontof_lm", "sino_small", "sino_clinical", "tof_sino", "osem",
+                             "profile_case", "profile_osem"])
     ap.add_argument("--cpu-lors", type=int, default=200_000)
     ap.add_argument("--budget-gb", type=float, default=None)
     ap.add_argument("--no-graphs", action="store_true")

@@ -261,6 +261,29 @@ def test_batched_frames(ops, clinical_img, lm_events):
     assert fwd_err(p2[:10_000], p_or0) <= 2 * FWD_TOL
 
 
+@pytest.mark.parametrize("lpw", [0, 4, 32])
+def test_nontof_lm_batch(ops, clinical_img, lm_events, lpw):
+    """Non-TOF listmode: the events of two frames (TOF bins dropped) in one
+    batched plan without TOF keys, as the non-TOF listmode benchmark runs
+    them; each frame against the oracle on its own image."""
+    g = synth.GEOM_CLINICAL
+    xs, xe, _ = lm_events
+    cuts = [0, 90_001, 200_000]
+    imgs = np.stack([clinical_img, 0.25 + clinical_img[:, ::-1].copy()])
+    ys = synth.uniform_values(cuts[-1], 7101, 0.5, 1.5)
+    plan = ops.jp_plan_create_batch(cuda(xs[:cuts[-1]]), cuda(xe[:cuts[-1]]), g, cuts, lors_per_warp=lpw)
+    p = ops.jp_fwd(plan, cuda(imgs)).cpu().numpy()
+    out = torch.zeros((2,) + g.shape, device="cuda")
+    ops.jp_back(plan, cuda(ys), out)
+    out = out.cpu().numpy()
+    for f in range(2):
+        a, b = cuts[f], cuts[f + 1]
+        p_or = oracle.fwd(xs[a:b], xe[a:b], imgs[f], g, "nontof", threads=THREADS)
+        assert fwd_err(p[a:b], p_or) <= FWD_TOL
+        b_or = oracle.back(xs[a:b], xe[a:b], ys[a:b], g, "nontof", threads=THREADS)
+        assert rel_l2(out[f], b_or) <= BACK_TOL
+
+
 def test_osem_elementwise(ops):
     rng = np.random.Generator(np.random.PCG64(8001))
     p = rng.uniform(0, 5, size=100_003).astype(np.float32)
