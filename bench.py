@@ -283,7 +283,8 @@ def run_ours(args):
     serving = None
     if not args.no_serving and rank == 0 and not nontof:
         rates = [float(r) for r in args.serving_rates.split(",")]
-        serving = run_serving(n_requests=args.serving_requests, rates=rates, max_slots=args.serving_slots)
+        serving = run_serving(n_requests=args.serving_requests, rates=rates, max_slots=args.serving_slots,
+                              fwhm_mm=args.fwhm)
 
     if rank == 0:
         peaks, peak_kind = measured_peaks()
@@ -539,7 +540,7 @@ def run_profile_osem(args):
     ph = synth.ellipsoid_phantom(g, synth.PHANTOM_CLINICAL, 5010, device=dev)
     xs, xe, tb = synth.lm_events(ph, g, synth.SCANNER_CLINICAL, tof, args.events, seed=5011, device=dev)
     sens = torch.ones(g.shape, device=dev)
-    spec = osem.FrameSpec(xs, xe, tb, g, synth.background_level(ph, tof))
+    spec = osem.FrameSpec(xs, xe, tb, g, synth.background_level(ph, tof), fwhm_mm=args.fwhm)
     fr = osem.LMOSEMFrame(spec, sens, tof)
     fr.run()
     torch.cuda.synchronize()
@@ -576,32 +577,68 @@ def run_profile_case(args):
 # ---------------------------------------------------------------------------
 # served listmode OSEM (frame stream): batched vs sequential plain
 # ---------------------------------------------------------------------------
+def time_gauss3d(g, fwhm_mm, reps=200):
+    """Device time of one resolution-model convolution H x (three separable
+    passes) of one image, and the bytes each pass moves at minimum (read +
+    write of the image; the image stays in L2 between passes)."""
+    from paper_2212_12519_gb300 import ops
+    x = torch.rand(g.shape, device="cuda")
+    out, work = torch.empty_like(x), torch.empty_like(x)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            ops.jp_gauss3d(x, g, fwhm_mm, out=out, work=work)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    # captured in a CUDA graph, as the OSEM iterations run, so host launch
+    # cost does not enter the device time
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        for _ in range(reps):
+            ops.jp_gauss3d(x, g, fwhm_mm, out=out, work=work)
+    graph.replay()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    graph.replay()
+    b.record()
+    torch.cuda.synchronize()
+    us = a.elapsed_time(b) * 1e3 / reps
+    nbytes = 3 * 2 * 4 * x.numel()
+    return {"image": list(g.shape), "us_per_convolution": us, "passes": 3,
+            "min_bytes_per_convolution": nbytes, "GBps_effective": nbytes / (us * 1e-6) / 1e9}
+
+
 def run_serving(n_requests=200, rates=(1.0,), pool_events=20_000_000, max_slots=4, budget_gb=None,
-                use_graphs=True, seed=5001):
+                use_graphs=True, seed=5001, fwhm_mm=4.5):
     from paper_2212_12519_gb300 import osem, serve, synth
     tof = synth.TOF_CLINICAL
     t0 = time.perf_counter()
     pools = serve.make_event_pools(tof, pool_events=pool_events)
     sens, checks = {}, {}
     for shape, pool in pools.items():
-        sens[shape], checks[str(shape)] = osem.sensitivity(pool["geom"])
+        s, checks[str(shape)] = osem.sensitivity(pool["geom"])
+        sens[shape] = osem.resolution_sensitivity(s, pool["geom"], fwhm_mm)
     setup_s = time.perf_counter() - t0
     geoms = [p["geom"] for p in pools.values()]
+    res_model = time_gauss3d(synth.GEOM_CLINICAL, fwhm_mm) if fwhm_mm > 0 else None
     # mu_seq: sequential plain server, all requests available at once
-    reqs = serve.make_requests(pools, n_requests, rate=1e9, seed=seed)
+    reqs = serve.make_requests(pools, n_requests, rate=1e9, seed=seed, fwhm_mm=fwhm_mm)
     seq = serve.OSEMServer(sens, tof, mode="sequential")
     base = seq.run(reqs)
     mu = base["frames_per_s"]
     bat = serve.OSEMServer(sens, tof, mode="batched", max_slots=max_slots, use_graphs=use_graphs,
                            hbm_budget=None if budget_gb is None else int(budget_gb * 2 ** 30))
-    bat.reserve(int(2e7), geoms)
+    bat.reserve(int(2e7), geoms, fwhm_mm=fwhm_mm)
     serve.reset(reqs)
     cap = bat.run(reqs)
     out = {"requests": n_requests, "mu_seq_frames_per_s": mu, "batched_capacity_frames_per_s": cap["frames_per_s"],
-           "sensitivity_fp64_check": checks, "setup_s": setup_s, "sweep": []}
+           "sensitivity_fp64_check": checks, "setup_s": setup_s, "resolution_fwhm_mm": fwhm_mm,
+           "resolution_model": res_model, "sweep": []}
     for f in rates:
         lam = f * mu
-        reqs = serve.make_requests(pools, n_requests, rate=lam, seed=seed)
+        reqs = serve.make_requests(pools, n_requests, rate=lam, seed=seed, fwhm_mm=fwhm_mm)
         r_seq = seq.run(reqs)
         serve.reset(reqs)
         r_bat = bat.run(reqs)
@@ -719,6 +756,7 @@ def main():
     ap.add_argument("--no-graphs", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--serving-slots", type=int, default=4)
+    ap.add_argument("--fwhm", type=float, default=4.5, help="OSEM resolution model FWHM in mm (0: none)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -734,7 +772,7 @@ def main():
         ops.load()
         rates = [float(r) for r in args.serving_rates.split(",")]
         out = run_serving(n_requests=args.serving_requests, rates=rates, max_slots=args.serving_slots,
-                          budget_gb=args.budget_gb, use_graphs=not args.no_graphs)
+                          budget_gb=args.budget_gb, use_graphs=not args.no_graphs, fwhm_mm=args.fwhm)
         print(json.dumps({"metric": "served listmode OSEM frames/s; p50/p99 latency", "workload": "osem_stream",
                           **out}), flush=True)
     else:

@@ -247,6 +247,54 @@ int jp_osem_subset_tof_lm_dev(jp_plan p, int32_t f0, int32_t f1, float* x, const
                               float sens_scale, const float* b_dev, const jp_tof* t, void* stream);
 
 /*
+ * Image-based resolution model H (paper Sec. 3: every listmode OSEM
+ * reconstruction applies a shift-invariant isotropic 3D Gaussian of 4.5 mm
+ * FWHM in image space; Sec. 5: two such convolutions per subset).  The
+ * paper fixes no discretisation; this library uses: per axis a,
+ * sigma_a = fwhm_mm[a] / sqrt(8 ln 2); taps = the Gaussian sampled at t*d_a
+ * (d_a the voxel size) for |t| <= R_a = ceil(truncate * sigma_a / d_a),
+ * normalised to sum 1 (fwhm 0: the single tap 1); the 3D kernel is the
+ * product of the axis kernels; the image is zero outside its grid, so H is
+ * symmetric (H^T = H).
+ */
+typedef struct jp_resolution {
+  float fwhm_mm[3]; /* per-axis FWHM in mm, >= 0 (4.5 on every axis in the paper) */
+  float truncate;   /* support half-width in sigmas, > 0 (4 is the usual value) */
+} jp_resolution;
+
+#define JP_MAX_RES_RADIUS 32 /* largest R_a in voxels */
+
+/*
+ * jp_gauss3d -- out = H img for n_images images of geometry g, each
+ * nvox = n0*n1*n2 float32 (index (i0*n1 + i1)*n2 + i2), images back to back.
+ *   work   device float32 scratch of n_images * nvox, caller-owned
+ *   img, out and work are device pointers, 4-byte aligned and pairwise
+ *   disjoint; n_images = 0 is a no-op.  Three separable passes (axis 2, 1,
+ *   0), each one kernel, FP32 accumulation in ascending tap order.
+ * Errors: JP_ERR_ARG (NULL or overlapping arrays, n_images < 0, fwhm < 0 or
+ * not finite, truncate <= 0, a radius above JP_MAX_RES_RADIUS), JP_ERR_ALIGN,
+ * JP_ERR_CUDA.
+ */
+int jp_gauss3d(const float* img, float* out, float* work, int32_t n_images, const jp_image_geom* g,
+               const jp_resolution* r, void* stream);
+
+/*
+ * jp_osem_subset_tof_lm_res -- listmode OSEM subset update with the
+ * resolution model (paper Sec. 3):
+ *   x[j] <- sens[j] > 0 ? x[j] * (H^T A_S^T (1 / (A_S H x + b)))[j] / (sens[j] * sens_scale) : 0
+ * where sens is the caller's H^T A^T 1.  Plan, frame range and TOF rules as
+ * jp_osem_subset_tof_lm; b_dev non-NULL reads b from device memory and the
+ * event range from the plan's device offsets (CUDA-graph capturable, as
+ * jp_osem_subset_tof_lm_dev), otherwise the scalar b is used.
+ *   work  device float32 scratch of 2 * nvox, caller-owned, disjoint from x
+ *         and sens.
+ * Errors: those of jp_osem_subset_tof_lm and jp_gauss3d.
+ */
+int jp_osem_subset_tof_lm_res(jp_plan p, int32_t f0, int32_t f1, float* x, const float* sens,
+                              float sens_scale, float b, const float* b_dev, const jp_tof* t,
+                              const jp_resolution* r, float* work, void* stream);
+
+/*
  * Listmode Poisson log-likelihood of a forward projection p (the training
  * objective of unrolled reconstruction networks, paper Sec. 4):
  *   jp_poisson_loglik_value: *value (device double) = sum_e w_e log(p_e + b_f)

@@ -1,4 +1,5 @@
-"""FP64 CPU oracle for Joseph forward/back projection (paper Sec. 2.1-2.2).
+"""FP64 CPU oracle for Joseph forward/back projection (paper Sec. 2.1-2.2),
+listmode OSEM and the image-based resolution model (Sec. 2.6, 3).
 
 TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
 the CPU-baseline leg of ``bench.py`` may import or run anything in this
@@ -12,3 +13,4 @@ from .joseph import (  # noqa: F401
     build, fwd, back, tof_weight, principal_axis, load, MODES,
 )
 from .osem import lm_osem_subset_update, lm_osem, poisson_loglik_grad  # noqa: F401
+from .resolution import gauss3d, gauss_taps, sigma_from_fwhm  # noqa: F401

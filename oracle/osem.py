@@ -6,24 +6,35 @@ s = A^T 1 over all possible LORs, subset S of n_sub event subsets, additive
 background b and unit event values,
     x <- x / (s / n_sub) * A_S^T ( 1 / (A_S x + b) ),   x = 0 where s = 0.
 Subset m holds the events e with e mod n_sub == m.
+
+With the image-based resolution model H (``fwhm_mm`` > 0, see
+``resolution.py``) the update is
+    x <- x / (s' / n_sub) * H^T A_S^T ( 1 / (A_S H x + b) )
+and ``sens`` is the caller's s' = H^T A^T 1.
 """
 from __future__ import annotations
 
 import numpy as np
 
-from . import joseph
+from . import joseph, resolution
 
 
 def _subset(arrs, m, n_sub):
     return [None if a is None else np.asarray(a)[m::n_sub] for a in arrs]
 
 
-def lm_osem_subset_update(x, xs, xe, tof_bin, geom, tof, sens, b, m, n_sub, threads=1):
-    """One subset update of TOF listmode OSEM (double precision)."""
+def lm_osem_subset_update(x, xs, xe, tof_bin, geom, tof, sens, b, m, n_sub, threads=1, fwhm_mm=0.0,
+                          truncate=4.0):
+    """One subset update of TOF listmode OSEM (double precision), with the
+    resolution model when ``fwhm_mm`` > 0."""
     sxs, sxe, stb = _subset([xs, xe, tof_bin], m, n_sub)
-    p = joseph.fwd(sxs, sxe, x, geom, mode="tof_lm", tof=tof, tof_bin=stb, threads=threads)
+    res = np.any(np.asarray(fwhm_mm, dtype=np.float64) > 0)
+    y = resolution.gauss3d(x, geom, fwhm_mm, truncate) if res else x
+    p = joseph.fwd(sxs, sxe, y, geom, mode="tof_lm", tof=tof, tof_bin=stb, threads=threads)
     q = 1.0 / (p + b)
     bp = joseph.back(sxs, sxe, q, geom, mode="tof_lm", tof=tof, tof_bin=stb, threads=threads)
+    if res:
+        bp = resolution.gauss3d(bp, geom, fwhm_mm, truncate, adjoint=True)
     s = np.asarray(sens, dtype=np.float64) / n_sub
     out = np.zeros_like(np.asarray(x, dtype=np.float64))
     pos = s > 0
@@ -31,13 +42,15 @@ def lm_osem_subset_update(x, xs, xe, tof_bin, geom, tof, sens, b, m, n_sub, thre
     return out
 
 
-def lm_osem(xs, xe, tof_bin, geom, tof, sens, b, n_iter, n_sub, threads=1, x0=None):
+def lm_osem(xs, xe, tof_bin, geom, tof, sens, b, n_iter, n_sub, threads=1, x0=None, fwhm_mm=0.0,
+            truncate=4.0):
     """Full TOF listmode OSEM: x0 = 1 on voxels with s > 0 (else 0)."""
     sens = np.asarray(sens, dtype=np.float64)
     x = (sens > 0).astype(np.float64) if x0 is None else np.asarray(x0, dtype=np.float64).copy()
     for _ in range(n_iter):
         for m in range(n_sub):
-            x = lm_osem_subset_update(x, xs, xe, tof_bin, geom, tof, sens, b, m, n_sub, threads)
+            x = lm_osem_subset_update(x, xs, xe, tof_bin, geom, tof, sens, b, m, n_sub, threads, fwhm_mm,
+                                      truncate)
     return x
 
 

@@ -44,6 +44,20 @@ class JosephNonTOF(torch.autograd.Function):
         return g, None
 
 
+class GaussianResolution(torch.autograd.Function):
+    """y = H x, the image-based resolution model (separable Gaussian of
+    ``fwhm_mm``, zero outside the grid); backward is H^T = H (symmetric taps)."""
+
+    @staticmethod
+    def forward(ctx, x, geom, fwhm_mm, truncate=4.0):
+        ctx.geom, ctx.fwhm, ctx.truncate = geom, fwhm_mm, truncate
+        return ops.jp_gauss3d(x.contiguous(), geom, fwhm_mm, truncate)
+
+    @staticmethod
+    def backward(ctx, g):
+        return ops.jp_gauss3d(g.contiguous(), ctx.geom, ctx.fwhm, ctx.truncate), None, None, None
+
+
 def tof_lm_project(x, plan, tof):
     return JosephTOFLM.apply(x, plan, tof)
 

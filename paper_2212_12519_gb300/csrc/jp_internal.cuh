@@ -55,6 +55,26 @@ int make_geom(const jp_image_geom* g, DevGeom* out);
 int make_tof(const jp_tof* t, bool sino, DevTof* out);
 
 // ---------------------------------------------------------------------------
+// image-based resolution model (separable Gaussian, jp_res.cu)
+// ---------------------------------------------------------------------------
+constexpr int kMaxResTaps = 2 * JP_MAX_RES_RADIUS + 1;
+
+struct GaussTaps {
+  int r[3];                    // radius R_a per axis
+  float w[3][kMaxResTaps];     // normalised taps, index t + R_a
+};
+
+int make_taps(const jp_image_geom* g, const jp_resolution* r, GaussTaps* out);
+
+// Three passes in -> b1 (axis 2) -> b2 (axis 1) -> dst (axis 0) over n_img
+// images; in != b1, b1 != b2, b2 != dst (in == b2 is allowed: pass 1 has
+// consumed it).  With upd_sens non-NULL the last pass is the OSEM update
+// dst[j] <- upd_sens[j]*scale > 0 ? dst[j] * (H in)[j] / (upd_sens[j]*scale) : 0
+// (one sensitivity image shared by the n_img images).
+int gauss_passes(const float* in, float* b1, float* b2, float* dst, int n_img, const DevGeom& g,
+                 const GaussTaps& t, const float* upd_sens, float scale, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
 // per-LOR setup (paper Sec. 2.1): principal axis, plane range, affine maps
 // ---------------------------------------------------------------------------
 struct Ray {

@@ -590,34 +590,48 @@ __global__ void __launch_bounds__(kMaxBlock) osem_kernel(const ProjParams p) {
   }
 }
 
-// x[v] <- s[v] > 0 ? x[v] * bp[v] / (s[v] * scale) : 0, with bp folded from
-// the back-projection quads (p.quads_bp, plane-fastest)
-__global__ void osem_update_kernel(const ProjParams p, float* __restrict__ x) {
-  const int32_t* used = p.axis_used;
-  bool use[3];
-  for (int a = 0; a < 3; ++a) use[a] = slot_axis_used(used, 0, a, 1, p.n_frames);
+// bp[v] folded from the back-projection quads (p.quads_bp, plane-fastest):
+// the 4 quad slots that hold voxel v, over the axes the subset used
+__device__ __forceinline__ float fold_bp(const ProjParams& p, const bool use[3], int64_t v) {
   const DevGeom& g = p.g;
-  const int64_t nvox = (int64_t)g.n[0] * g.n[1] * g.n[2];
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvox; v += (int64_t)gridDim.x * blockDim.x) {
-    const int i0 = (int)(v / g.stride[0]);
-    const int r0 = (int)(v - (int64_t)i0 * g.stride[0]);
-    const int i1 = r0 / g.n[2], i2 = r0 - (r0 / g.n[2]) * g.n[2];
-    float bp = 0.f;
+  const int i0 = (int)(v / g.stride[0]);
+  const int r0 = (int)(v - (int64_t)i0 * g.stride[0]);
+  const int i1 = r0 / g.n[2], i2 = r0 - (r0 / g.n[2]) * g.n[2];
+  float bp = 0.f;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      if (!use[a]) continue;
-      const int k = (a == 0) ? i0 : (a == 1 ? i1 : i2);
-      const int I = (a == 0) ? i1 : i0;
-      const int J = (a == 2) ? i1 : i2;
-      const int nc2 = p.ql.nc2[a], nb2 = p.ql.nb2[a];
-      const int na = p.ql.nap[a];
-      const float4* Q = p.quads_bp + p.ql.base[a];
-      bp += Q[quad_index(true, k, I + 1, J + 1, na, nb2, nc2)].x + Q[quad_index(true, k, I, J + 1, na, nb2, nc2)].y +
-            Q[quad_index(true, k, I + 1, J, na, nb2, nc2)].z + Q[quad_index(true, k, I, J, na, nb2, nc2)].w;
-    }
+  for (int a = 0; a < 3; ++a) {
+    if (!use[a]) continue;
+    const int k = (a == 0) ? i0 : (a == 1 ? i1 : i2);
+    const int I = (a == 0) ? i1 : i0;
+    const int J = (a == 2) ? i1 : i2;
+    const int nc2 = p.ql.nc2[a], nb2 = p.ql.nb2[a];
+    const int na = p.ql.nap[a];
+    const float4* Q = p.quads_bp + p.ql.base[a];
+    bp += Q[quad_index(true, k, I + 1, J + 1, na, nb2, nc2)].x + Q[quad_index(true, k, I, J + 1, na, nb2, nc2)].y +
+          Q[quad_index(true, k, I + 1, J, na, nb2, nc2)].z + Q[quad_index(true, k, I, J, na, nb2, nc2)].w;
+  }
+  return bp;
+}
+
+// x[v] <- s[v] > 0 ? x[v] * bp[v] / (s[v] * scale) : 0
+__global__ void osem_update_kernel(const ProjParams p, float* __restrict__ x) {
+  bool use[3];
+  for (int a = 0; a < 3; ++a) use[a] = slot_axis_used(p.axis_used, 0, a, 1, p.n_frames);
+  const int64_t nvox = (int64_t)p.g.n[0] * p.g.n[1] * p.g.n[2];
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvox; v += (int64_t)gridDim.x * blockDim.x) {
+    const float bp = fold_bp(p, use, v);
     const float sv = p.sens[v] * p.sens_scale;
     x[v] = sv > 0.f ? x[v] * bp / sv : 0.f;
   }
+}
+
+// z[v] = bp[v] (resolution-model path: H^T is applied to bp before the update)
+__global__ void osem_fold_kernel(const ProjParams p, float* __restrict__ z) {
+  bool use[3];
+  for (int a = 0; a < 3; ++a) use[a] = slot_axis_used(p.axis_used, 0, a, 1, p.n_frames);
+  const int64_t nvox = (int64_t)p.g.n[0] * p.g.n[1] * p.g.n[2];
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvox; v += (int64_t)gridDim.x * blockDim.x)
+    z[v] = fold_bp(p, use, v);
 }
 
 // ---------------------------------------------------------------------------
@@ -1112,8 +1126,11 @@ extern "C" int jp_count_samples(jp_plan pl, int32_t mode, const jp_tof* t, uint6
 
 namespace jp {
 namespace {
+// One listmode-OSEM subset update; with res non-NULL the resolution model H
+// wraps the projections (x -> H x before the forward projection, H^T on the
+// back projection before the update), using work[0 .. 2 nvox).
 int osem_subset(jp_plan pl, int32_t f0, int32_t f1, float* x, const float* sens, float sens_scale, float b,
-                const float* b_dev, const jp_tof* t, void* stream) {
+                const float* b_dev, const jp_tof* t, const jp_resolution* res, float* work, void* stream) {
   clear_error();
   if (!pl) return fail(JP_ERR_ARG, "plan is NULL");
   if (!(pl->opts.flags & JP_PLAN_INTERLEAVED)) return fail(JP_ERR_STATE, "OSEM subsets need a JP_PLAN_INTERLEAVED plan");
@@ -1129,6 +1146,22 @@ int osem_subset(jp_plan pl, int32_t f0, int32_t f1, float* x, const float* sens,
   if (rc) return rc;
   rc = make_tof(t, false, &p.tof);
   if (rc) return rc;
+  const int64_t nvox = (int64_t)p.g.n[0] * p.g.n[1] * p.g.n[2];
+  GaussTaps taps;
+  float *wy = nullptr, *wt = nullptr;
+  if (res) {
+    rc = make_taps(&pl->g, res, &taps);
+    if (rc) return rc;
+    if (!work) return fail(JP_ERR_ARG, "work is NULL");
+    if (!aligned(work, 4)) return fail(JP_ERR_ALIGN, "work must be 4-byte aligned");
+    const uintptr_t w0 = reinterpret_cast<uintptr_t>(work), w1 = w0 + 2 * nvox * sizeof(float);
+    const uintptr_t xa = reinterpret_cast<uintptr_t>(x), sa = reinterpret_cast<uintptr_t>(sens);
+    const uintptr_t nb = nvox * sizeof(float);
+    if ((xa < w1 && w0 < xa + nb) || (sa < w1 && w0 < sa + nb))
+      return fail(JP_ERR_ARG, "work must not overlap x or sens");
+    wy = work;
+    wt = work + nvox;
+  }
   p.lor = pl->lor;
   p.perm = pl->perm;
   p.frame_off = pl->frame_off_dev;
@@ -1141,6 +1174,13 @@ int osem_subset(jp_plan pl, int32_t f0, int32_t f1, float* x, const float* sens,
   p.shared = 1;
   p.kfast = 1;
   p.img_in = x;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (res) {
+    // y = H x (passes x -> y -> t -> y); the forward projection reads y
+    rc = gauss_passes(x, wy, wt, wy, 1, p.g, taps, nullptr, 0.f, st);
+    if (rc) return rc;
+    p.img_in = wy;
+  }
   p.quads = pl->quads;
   p.quads_bp = pl->quads + pl->ql.slot;
   p.bg = b;
@@ -1149,7 +1189,6 @@ int osem_subset(jp_plan pl, int32_t f0, int32_t f1, float* x, const float* sens,
   p.sens_scale = sens_scale;
   p.counter = pl->work_counter;
   p.perm_in_rec = pl->has_delta ? 0 : 1;
-  cudaStream_t st = (cudaStream_t)stream;
   const int64_t max_quad = std::max(std::max(p.ql.size[0], p.ql.size[1]), p.ql.size[2]);
   dim3 qgrid(aux_grid(max_quad, 256), 3);
   quad_build_kernel<<<qgrid, 256, 0, st>>>(p);
@@ -1185,7 +1224,14 @@ int osem_subset(jp_plan pl, int32_t f0, int32_t f1, float* x, const float* sens,
     else rc = (lpw == 1) ? pick(osem_kernel<false, 32>) : (lpw == 2 ? pick(osem_kernel<false, 16>) : pick(osem_kernel<false, 8>));
     if (rc) return rc;
   }
-  const int64_t nvox = (int64_t)p.g.n[0] * p.g.n[1] * p.g.n[2];
+  if (res) {
+    // z = fold(bp) into t; x <- x * (H^T z) / (s scale) on the last pass
+    // (passes t -> y -> t -> x; H^T = H for the symmetric taps)
+    osem_fold_kernel<<<aux_grid(nvox, 256), 256, 0, st>>>(p, wt);
+    count_launch();
+    JP_TRY_CUDA(cudaGetLastError());
+    return gauss_passes(wt, wy, wt, x, 1, p.g, taps, sens, sens_scale, st);
+  }
   osem_update_kernel<<<aux_grid(nvox, 256), 256, 0, st>>>(p, x);
   count_launch();
   JP_TRY_CUDA(cudaGetLastError());
@@ -1196,7 +1242,7 @@ int osem_subset(jp_plan pl, int32_t f0, int32_t f1, float* x, const float* sens,
 
 extern "C" int jp_osem_subset_tof_lm(jp_plan pl, int32_t f0, int32_t f1, float* x, const float* sens,
                                      float sens_scale, float b, const jp_tof* t, void* stream) {
-  return osem_subset(pl, f0, f1, x, sens, sens_scale, b, nullptr, t, stream);
+  return osem_subset(pl, f0, f1, x, sens, sens_scale, b, nullptr, t, nullptr, nullptr, stream);
 }
 
 extern "C" int jp_osem_subset_tof_lm_dev(jp_plan pl, int32_t f0, int32_t f1, float* x, const float* sens,
@@ -1205,7 +1251,17 @@ extern "C" int jp_osem_subset_tof_lm_dev(jp_plan pl, int32_t f0, int32_t f1, flo
     clear_error();
     return fail(JP_ERR_ARG, "b_dev is NULL");
   }
-  return osem_subset(pl, f0, f1, x, sens, sens_scale, 0.f, b_dev, t, stream);
+  return osem_subset(pl, f0, f1, x, sens, sens_scale, 0.f, b_dev, t, nullptr, nullptr, stream);
+}
+
+extern "C" int jp_osem_subset_tof_lm_res(jp_plan pl, int32_t f0, int32_t f1, float* x, const float* sens,
+                                         float sens_scale, float b, const float* b_dev, const jp_tof* t,
+                                         const jp_resolution* r, float* work, void* stream) {
+  if (!r) {
+    jp::clear_error();
+    return jp::fail(JP_ERR_ARG, "resolution parameters are NULL");
+  }
+  return osem_subset(pl, f0, f1, x, sens, sens_scale, b, b_dev, t, r, work, stream);
 }
 
 extern "C" int jp_fwd(jp_plan p, const float* img, int64_t s, float* proj, void* st) {

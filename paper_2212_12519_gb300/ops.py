@@ -42,6 +42,10 @@ class TofC(ctypes.Structure):
     _fields_ = [("bin_width", F32), ("sigma", F32), ("n_sigmas", F32), ("n_bins", I32)]
 
 
+class ResolutionC(ctypes.Structure):
+    _fields_ = [("fwhm_mm", F32 * 3), ("truncate", F32)]
+
+
 class PlanOptsC(ctypes.Structure):
     _fields_ = [("block", I32), ("slope_bins", I32), ("offset_bins", I32), ("window_bins", I32),
                 ("tof_bin_width", F32), ("lors_per_warp", I32), ("flags", I32), ("zoff_bins", I32),
@@ -72,6 +76,8 @@ _SIGS = {
     "jp_osem_subset_tof_lm": [P, I32, I32, P, P, F32, F32, P, P],
     "jp_osem_init": [P, P, I64, P],
     "jp_osem_subset_tof_lm_dev": [P, I32, I32, P, P, F32, P, P, P],
+    "jp_osem_subset_tof_lm_res": [P, I32, I32, P, P, F32, F32, P, P, P, P, P],
+    "jp_gauss3d": [P, P, P, I32, P, P, P],
     "jp_poisson_loglik_value": [P, P, P, P, I64, P, P],
     "jp_poisson_loglik_grad": [P, P, P, P, P, I64, P, P],
     "jp_back_tof_lm_noalloc": [P, P, P, P, I64, P, P, P, P, P],
@@ -137,6 +143,18 @@ def image_geom(geom) -> ImageGeomC:
         g.origin[i] = float(geom.origin[i])
         g.voxsize[i] = float(geom.voxsize[i])
     return g
+
+
+def resolution(fwhm_mm, truncate: float = 4.0) -> ResolutionC:
+    """jp_resolution of a scalar (isotropic) or per-axis FWHM in mm."""
+    f = [float(fwhm_mm)] * 3 if isinstance(fwhm_mm, (int, float)) else [float(v) for v in fwhm_mm]
+    if len(f) != 3:
+        raise ValueError("fwhm_mm must be a scalar or three values")
+    r = ResolutionC()
+    for i in range(3):
+        r.fwhm_mm[i] = f[i]
+    r.truncate = float(truncate)
+    return r
 
 
 def tof_params(tof) -> TofC:
@@ -389,6 +407,43 @@ def jp_osem_subset_tof_lm_dev(plan: Plan, f0: int, f1: int, x, sens, sens_scale:
                                             _ptr(sens, torch.float32, "sens"), float(sens_scale),
                                             _ptr(b_dev, torch.float32, "b"), ctypes.byref(t), _stream(stream)))
     return x
+
+
+def jp_osem_subset_tof_lm_res(plan: Plan, f0: int, f1: int, x, sens, sens_scale: float, b, tof, fwhm_mm,
+                              work, truncate: float = 4.0, stream=None):
+    """Subset update with the resolution model H (Gaussian of ``fwhm_mm``):
+    x <- x / (sens*sens_scale) * H^T A_S^T (1/(A_S H x + b)), sens = H^T A^T 1.
+    ``b`` is a float, or a device float tensor (read when the kernels run,
+    capturable in a CUDA graph); ``work`` holds 2 images."""
+    t = tof_params(tof)
+    r = resolution(fwhm_mm, truncate)
+    b_dev = b if isinstance(b, torch.Tensor) else None
+    _check(load().jp_osem_subset_tof_lm_res(plan.handle, int(f0), int(f1), _ptr(x, torch.float32, "x"),
+                                            _ptr(sens, torch.float32, "sens"), float(sens_scale),
+                                            0.0 if b_dev is not None else float(b),
+                                            _ptr(b_dev, torch.float32, "b"), ctypes.byref(t), ctypes.byref(r),
+                                            _ptr(work, torch.float32, "work"), _stream(stream)))
+    return x
+
+
+def jp_gauss3d(img, geom, fwhm_mm, truncate: float = 4.0, out=None, work=None, stream=None):
+    """out = H img: separable Gaussian resolution model of ``fwhm_mm`` (zero
+    outside the grid; H^T = H).  ``img`` is one image of ``geom.shape`` or a
+    stack [n, *geom.shape]."""
+    shape = tuple(int(v) for v in geom.shape)
+    if tuple(img.shape[-3:]) != shape or img.dim() not in (3, 4):
+        raise ValueError("img must be [*geom.shape] or [n, *geom.shape]")
+    n = 1 if img.dim() == 3 else int(img.shape[0])
+    out = torch.empty_like(img) if out is None else out
+    work = torch.empty_like(img) if work is None else work
+    if out.shape != img.shape or work.numel() < img.numel():
+        raise ValueError("out must match img and work must hold as many voxels")
+    g = image_geom(geom)
+    r = resolution(fwhm_mm, truncate)
+    _check(load().jp_gauss3d(_ptr(img, torch.float32, "img"), _ptr(out, torch.float32, "out"),
+                             _ptr(work, torch.float32, "work"), n, ctypes.byref(g), ctypes.byref(r),
+                             _stream(stream)))
+    return out
 
 
 def jp_poisson_loglik_value(plan: Optional[Plan], proj, w, b, out=None, stream=None):

@@ -1,6 +1,12 @@
 """Listmode OSEM on the GPU (paper Sec. 2.6 and 3: TOF listmode OSEM,
 x <- x / s_sub * A_S^T (1 / (A_S x + b)), subsets of the event stream).
 
+With the image-based resolution model of Sec. 3 (a 3D Gaussian of
+``fwhm_mm``, 4.5 mm in the paper) the projector is A H and the update
+x <- x / s'_sub * H^T A_S^T (1 / (A_S H x + b)) uses s' = H^T A^T 1
+(``resolution_sensitivity``); one call of jp_osem_subset_tof_lm_res runs both
+convolutions, the fused projections and the update.
+
 The sensitivity image s = A^T 1 is the non-TOF back projection of every LOR
 of the scanner's span-1 sinogram; a frame's events are held in one plan
 whose frames are the subsets e mod n_sub; one subset update is one call of
@@ -45,6 +51,14 @@ def sensitivity(geom: synth.ImageGeom, spec: synth.SinoSpec = synth.SINO_CLINICA
     return s, info
 
 
+def resolution_sensitivity(sens: torch.Tensor, geom: synth.ImageGeom, fwhm_mm: float) -> torch.Tensor:
+    """s' = H^T s for the resolution model (H^T = H: symmetric taps, zero
+    outside the grid)."""
+    if fwhm_mm <= 0:
+        return sens
+    return ops.jp_gauss3d(sens.contiguous(), geom, fwhm_mm)
+
+
 # Sort granularity of a frame's subset plan: the subsets multiply the key
 # space, so coarser bins than a single-frame plan keep the histogram small.
 OSEM_PLAN_OPTS = dict(slope_bins=64, offset_bins=128, window_bins=16, zoff_bins=4)
@@ -60,6 +74,7 @@ class FrameSpec:
     b: float
     n_iter: int = 3
     n_sub: int = 8
+    fwhm_mm: float = 0.0    # resolution model (0: none); sens must then be H^T A^T 1
 
 
 class LMOSEMFrame:
@@ -89,14 +104,20 @@ class LMOSEMFrame:
                                       for m in range(spec.n_sub + 1)]
                 self.plan = plan
             self.x = torch.empty(spec.geom.shape, dtype=torch.float32, device=spec.xs.device)
+            self.work = (torch.empty((2,) + tuple(spec.geom.shape), dtype=torch.float32, device=spec.xs.device)
+                         if spec.fwhm_mm > 0 else None)
             ops.jp_osem_init(self.x, sens)
         self.graph = None
 
     def _updates(self, n_iter):
         for _ in range(n_iter):
             for m in range(self.spec.n_sub):
-                ops.jp_osem_subset_tof_lm(self.plan, m, m + 1, self.x, self.sens, 1.0 / self.spec.n_sub,
-                                          self.spec.b, self.tof)
+                if self.work is not None:
+                    ops.jp_osem_subset_tof_lm_res(self.plan, m, m + 1, self.x, self.sens, 1.0 / self.spec.n_sub,
+                                                  self.spec.b, self.tof, self.spec.fwhm_mm, self.work)
+                else:
+                    ops.jp_osem_subset_tof_lm(self.plan, m, m + 1, self.x, self.sens, 1.0 / self.spec.n_sub,
+                                              self.spec.b, self.tof)
 
     def run(self):
         """All n_iter x n_sub subset updates, launched on the frame's stream."""
@@ -142,17 +163,18 @@ def estimate_bytes(n_events: int, geom: synth.ImageGeom, n_sub: int = 8,
                    slope_bins=64, offset_bins=128, window_bins=16, zoff_bins=4) -> int:
     """Device bytes a frame holds while it is being reconstructed: its
     events, its plan (packed events, permutation, keys, histogram) and the
-    image workspace."""
+    image workspace (with the resolution model's two scratch images)."""
     n0, n1, n2 = geom.shape
     quad = 16 * (n0 * (n1 + 2) * (n2 + 2) + n1 * (n0 + 2) * (n2 + 2) + n2 * (n0 + 2) * (n1 + 2))
     hist = 4 * n_sub * 3 * slope_bins * offset_bins * window_bins * zoff_bins
-    return int(n_events * (26 + 36 + 4) + 2 * quad + hist + 8 * n0 * n1 * n2)
+    return int(n_events * (26 + 36 + 4) + 2 * quad + hist + 16 * n0 * n1 * n2)
 
 
 def reconstruct_plain(spec: FrameSpec, sens: torch.Tensor, tof: synth.TofParams) -> torch.Tensor:
     """Sequential plain per-frame OSEM: the planless one-thread-per-event
     kernels (the paper's own parallelisation), subset by subset, with the
-    element-wise ratio and update kernels."""
+    element-wise ratio and update kernels (and, with a resolution model, a
+    separate convolution before the forward and after the back projection)."""
     xs_s = [spec.xs[m::spec.n_sub].contiguous() for m in range(spec.n_sub)]
     xe_s = [spec.xe[m::spec.n_sub].contiguous() for m in range(spec.n_sub)]
     tb_s = [spec.tof_bin[m::spec.n_sub].contiguous() for m in range(spec.n_sub)]
@@ -161,11 +183,20 @@ def reconstruct_plain(spec: FrameSpec, sens: torch.Tensor, tof: synth.TofParams)
     bp = torch.empty_like(x)
     bvec = torch.full((1,), spec.b, dtype=torch.float32, device=x.device)
     nvox = x.numel()
+    res = spec.fwhm_mm > 0
+    y = torch.empty_like(x) if res else x
+    work = torch.empty_like(x) if res else None
     for _ in range(spec.n_iter):
         for m in range(spec.n_sub):
-            p = ops.jp_fwd_lors(xs_s[m], xe_s[m], x, spec.geom, "tof_lm", tof, tof_bin=tb_s[m])
+            if res:
+                ops.jp_gauss3d(x, spec.geom, spec.fwhm_mm, out=y, work=work)
+            p = ops.jp_fwd_lors(xs_s[m], xe_s[m], y, spec.geom, "tof_lm", tof, tof_bin=tb_s[m])
             ops.jp_osem_ratio(None, p, bvec)
             bp.zero_()
             ops.jp_back_lors(xs_s[m], xe_s[m], p, spec.geom, bp, "tof_lm", tof, tof_bin=tb_s[m])
-            ops.jp_osem_update(x, bp, sens, 1.0 / spec.n_sub, nvox)
+            if res:
+                ops.jp_gauss3d(bp, spec.geom, spec.fwhm_mm, out=y, work=work)
+                ops.jp_osem_update(x, y, sens, 1.0 / spec.n_sub, nvox)
+            else:
+                ops.jp_osem_update(x, bp, sens, 1.0 / spec.n_sub, nvox)
     return x

@@ -64,7 +64,7 @@ class OSEMServer:
         self.plans: Dict[tuple, ops.Plan] = {}
         self.slot_graphs: Dict[tuple, "SlotGraph"] = {}
 
-    def reserve(self, max_events: int, geoms: List[synth.ImageGeom], n_sub: int = 8):
+    def reserve(self, max_events: int, geoms: List[synth.ImageGeom], n_sub: int = 8, fwhm_mm: float = 0.0):
         """Pre-creates one interleaved plan per (slot, image grid) with room
         for ``max_events`` events, so admitting a frame only rebinds it (no
         device allocation, no device-wide synchronisation)."""
@@ -87,7 +87,8 @@ class OSEMServer:
                 del xs, tb
                 if self.use_graphs:
                     self.slot_graphs[(slot, g.shape)] = SlotGraph(
-                        self.plans[(slot, g.shape)], self.sens[g.shape], self.tof, g, n_sub, self.streams[slot])
+                        self.plans[(slot, g.shape)], self.sens[g.shape], self.tof, g, n_sub, self.streams[slot],
+                        fwhm_mm)
 
     def close(self):
         self.slot_graphs.clear()
@@ -185,21 +186,30 @@ class SlotGraph:
     the slot's plan to a new frame keeps the graph valid."""
 
     def __init__(self, plan: ops.Plan, sens: torch.Tensor, tof: synth.TofParams, geom: synth.ImageGeom,
-                 n_sub: int, stream: torch.cuda.Stream):
+                 n_sub: int, stream: torch.cuda.Stream, fwhm_mm: float = 0.0):
         self.plan, self.sens, self.tof, self.n_sub, self.stream = plan, sens, tof, n_sub, stream
+        self.fwhm_mm = fwhm_mm
         self.x = torch.zeros(geom.shape, dtype=torch.float32, device="cuda")
         self.b = torch.zeros(1, dtype=torch.float32, device="cuda")
+        self.work = (torch.empty((2,) + tuple(geom.shape), dtype=torch.float32, device="cuda")
+                     if fwhm_mm > 0 else None)
         self.graph = torch.cuda.CUDAGraph()
         torch.cuda.synchronize()
         with torch.cuda.graph(self.graph, stream=stream):
             for m in range(n_sub):
-                ops.jp_osem_subset_tof_lm_dev(plan, m, m + 1, self.x, sens, 1.0 / n_sub, self.b, tof)
+                if self.work is not None:
+                    ops.jp_osem_subset_tof_lm_res(plan, m, m + 1, self.x, sens, 1.0 / n_sub, self.b, tof, fwhm_mm,
+                                                  self.work)
+                else:
+                    ops.jp_osem_subset_tof_lm_dev(plan, m, m + 1, self.x, sens, 1.0 / n_sub, self.b, tof)
         torch.cuda.synchronize()
 
     def run(self, spec: osem.FrameSpec) -> torch.Tensor:
         n = int(spec.xs.shape[0])
         if spec.n_sub != self.n_sub:
             raise ValueError("subset count differs from the captured graph")
+        if spec.fwhm_mm != self.fwhm_mm:
+            raise ValueError("resolution model differs from the captured graph")
         with torch.cuda.stream(self.stream):
             ops.jp_plan_rebind(self.plan, spec.xs, spec.xe, [0] * spec.n_sub + [n], tof_bin=spec.tof_bin)
             self.b.fill_(float(spec.b))
@@ -227,9 +237,11 @@ def make_event_pools(tof: synth.TofParams, pool_events: int = 20_000_000, device
 
 
 def make_requests(pools: dict, n_requests: int, rate: float, seed: int = 5001,
-                  ev_min: float = 1e5, ev_max: float = 2e7, n_iter: int = 3, n_sub: int = 8) -> List[Request]:
+                  ev_min: float = 1e5, ev_max: float = 2e7, n_iter: int = 3, n_sub: int = 8,
+                  fwhm_mm: float = 0.0) -> List[Request]:
     """Poisson arrivals at ``rate`` frames/s; events log-uniform in
-    [ev_min, ev_max]; image 128x128x71 or 200x200x71 with probability 1/2."""
+    [ev_min, ev_max]; image 128x128x71 or 200x200x71 with probability 1/2;
+    resolution model of ``fwhm_mm`` (0: none)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     gaps = rng.exponential(1.0 / rate, size=n_requests)
     arrivals = np.cumsum(gaps) - gaps[0]
@@ -242,7 +254,7 @@ def make_requests(pools: dict, n_requests: int, rate: float, seed: int = 5001,
         ne = min(ne, npool)
         off = int(rng.integers(0, npool - ne + 1))
         spec = osem.FrameSpec(pool["xs"][off:off + ne], pool["xe"][off:off + ne], pool["tb"][off:off + ne],
-                              pool["geom"], pool["b"], n_iter=n_iter, n_sub=n_sub)
+                              pool["geom"], pool["b"], n_iter=n_iter, n_sub=n_sub, fwhm_mm=fwhm_mm)
         reqs.append(Request(i, float(arrivals[i]), spec))
     return reqs
 

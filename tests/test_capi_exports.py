@@ -76,3 +76,35 @@ def test_host_argument_checks(lib):
     # bad OSEM arguments
     assert lib.jp_osem_update(P(16), P(16), P(16), ctypes.c_float(-1.0), ctypes.c_int64(4), 1,
                               ctypes.c_int64(4), ctypes.c_int64(0), None) == -1
+
+
+def test_resolution_model_argument_checks(lib):
+    """jp_gauss3d / jp_osem_subset_tof_lm_res reject bad input on the host."""
+    from paper_2212_12519_gb300 import ops
+    ops.load()
+    lib.jp_last_error.restype = ctypes.c_char_p
+    g = ops.ImageGeomC()
+    for i in range(3):
+        g.n[i] = 8
+        g.voxsize[i] = 2.0
+    P = ctypes.c_void_p
+    nb = 8 * 8 * 8 * 4
+
+    def call(r, img=4096, out=4096 + nb, work=4096 + 2 * nb, n=1):
+        return lib.jp_gauss3d(P(img), P(out), P(work), n, ctypes.byref(g), ctypes.byref(r), None)
+
+    ok = ops.resolution(4.5)
+    assert call(ops.resolution(4.5), n=0) == 0                      # nothing to do, no CUDA call
+    assert call(ops.resolution(-1.0)) == -1
+    assert call(ops.resolution((4.5, float("nan"), 4.5))) == -1
+    assert call(ops.resolution(4.5, truncate=0.0)) == -1
+    assert call(ops.resolution(200.0)) == -1                        # radius above 32 voxels
+    assert b"radius" in lib.jp_last_error()
+    assert call(ok, out=4096 + nb // 2) == -1                       # img and out overlap
+    assert b"overlap" in lib.jp_last_error()
+    assert call(ok, work=4096 + 4) == -1                            # work overlaps img
+    assert call(ok, out=4096 + nb + 2) == -2                        # misaligned
+    assert call(ok, n=-1) == -1
+    assert lib.jp_gauss3d(P(4096), P(4096 + nb), None, 1, ctypes.byref(g), ctypes.byref(ok), None) == -1
+    assert lib.jp_osem_subset_tof_lm_res(None, 0, 1, P(16), P(16), ctypes.c_float(1.0), ctypes.c_float(0.0),
+                                         None, None, None, P(16), None) == -1

@@ -531,3 +531,119 @@ def test_planted_mistakes_are_caught():
     for mutant in range(1, 8):
         oracle.joseph.build(mutant)
         assert _pins(mutant), f"planted mistake {mutant} not caught"
+
+
+# ---------------------------------------------------------------------------
+# image-based resolution model (paper Sec. 3: 3D Gaussian, 4.5 mm FWHM)
+# ---------------------------------------------------------------------------
+RES_FWHM = 4.5
+# voxels fine enough that the sampled Gaussian keeps the continuous moments
+# (Poisson summation: the error is ~exp(-2 pi^2 sigma^2 / d^2) < 1e-19), and
+# a grid that holds the whole 7-sigma support around its centre voxel
+RES_GEOM = G((23, 29, 25), (-13.75, -14.0, -14.4), (1.25, 1.0, 1.2))
+RES_CENTRE = (11, 14, 12)
+
+
+def _res_pins(mutant=0):
+    """Pins of oracle.gauss3d / gauss_taps; returns the names that failed."""
+    from oracle import resolution as R
+    failed = []
+    # (1) defining property of the FWHM: the normalised taps (truncated at
+    #     8 sigma, so their moments are the continuous ones) have unit mass,
+    #     zero mean, and a variance v with exp(-(FWHM/2)^2 / (2 v)) = 1/2
+    for d in (0.25, 0.6):
+        w = R.gauss_taps(RES_FWHM, (d, d, d), truncate=8.0, _mutant=mutant)[0]
+        r = (len(w) - 1) // 2
+        t = np.arange(-r, r + 1) * d
+        if abs(w.sum() - 1.0) > 1e-13 or abs(np.dot(w, t)) > 1e-12:
+            failed.append("taps-mass-mean")
+            break
+        v = float(np.dot(w, t * t))
+        if abs(math.exp(-0.5 * (RES_FWHM / 2) ** 2 / v) - 0.5) > 1e-10:
+            failed.append("taps-fwhm")
+            break
+    # (2) response to an interior delta, non-isotropic voxels: unit mass,
+    #     rank-one (separable) and, along every axis, the marginal's variance
+    #     in mm^2 is the same sigma^2 (the FWHM is isotropic in mm)
+    delta = np.zeros(RES_GEOM.shape)
+    c = RES_CENTRE
+    delta[c] = 1.0
+    h = R.gauss3d(delta, RES_GEOM, RES_FWHM, truncate=7.0, _mutant=mutant)
+    if abs(h.sum() - 1.0) > 1e-12:
+        failed.append("delta-mass")
+    variances = []
+    for a in range(3):
+        m = h.sum(axis=tuple(b for b in range(3) if b != a))
+        t = (np.arange(RES_GEOM.shape[a]) - c[a]) * RES_GEOM.voxsize[a]
+        variances.append(float(np.dot(m, t * t) / m.sum()))
+    v_true = (RES_FWHM / 2) ** 2 / (2 * math.log(2.0))  # half maximum at FWHM/2
+    if max(abs(v - v_true) for v in variances) > 1e-9 * v_true:
+        failed.append("delta-variance")
+    m0, m1, m2 = (h.sum(axis=(1, 2)), h.sum(axis=(0, 2)), h.sum(axis=(0, 1)))
+    if np.abs(h - np.einsum("i,j,k->ijk", m0, m1, m2)).max() > 1e-15:
+        failed.append("delta-separable")
+    # (3) special case that reduces to a library routine: the separable
+    #     correlation with scipy.ndimage.correlate1d (zero outside the grid)
+    import scipy.ndimage as ndi
+    rng = np.random.Generator(np.random.PCG64(131))
+    g2 = G((9, 12, 7), (-4.0, -6.0, -5.25), (2.0, 1.5, 3.0))
+    x = rng.uniform(0.0, 1.0, g2.shape)
+    taps = R.gauss_taps(RES_FWHM, g2.voxsize)
+    ref = x
+    for a in range(3):
+        ref = ndi.correlate1d(ref, taps[a], axis=a, mode="constant", cval=0.0)
+    if np.abs(R.gauss3d(x, g2, RES_FWHM, _mutant=mutant) - ref).max() > 1e-14:
+        failed.append("scipy-separable")
+    # (4) zero outside the grid: a corner delta keeps, per axis, the centre
+    #     tap and one half of the others, i.e. (1 + w_centre) / 2
+    corner = np.zeros(g2.shape)
+    corner[0, 0, 0] = 1.0
+    kept = np.prod([(1.0 + w[(len(w) - 1) // 2]) / 2.0 for w in taps])
+    if abs(R.gauss3d(corner, g2, RES_FWHM, _mutant=mutant).sum() - kept) > 1e-14:
+        failed.append("corner-mass")
+    return failed
+
+
+def test_resolution_model_pins():
+    assert _res_pins() == []
+
+
+def test_resolution_model_adjoint_and_identity():
+    from oracle import resolution as R
+    rng = np.random.Generator(np.random.PCG64(132))
+    g2 = G((10, 8, 13), (-3.0, -2.0, -6.0), (2.0, 2.5, 1.5))
+    x, y = rng.uniform(size=g2.shape), rng.uniform(size=g2.shape)
+    hx = R.gauss3d(x, g2, (4.5, 3.0, 6.0))
+    hty = R.gauss3d(y, g2, (4.5, 3.0, 6.0), adjoint=True)
+    assert float(np.sum(hx * y)) == pytest.approx(float(np.sum(x * hty)), rel=1e-13)
+    # symmetric taps: H^T = H
+    assert np.abs(hty - R.gauss3d(y, g2, (4.5, 3.0, 6.0))).max() < 1e-15
+    # FWHM 0 is the identity
+    assert np.array_equal(R.gauss3d(x, g2, 0.0), x)
+    # a stack of images is filtered image by image
+    st = R.gauss3d(np.stack([x, y]), g2, 4.5)
+    assert np.array_equal(st[1], R.gauss3d(y, g2, 4.5))
+
+
+def test_resolution_model_planted_mistakes():
+    for mutant in (1, 2, 3, 4):
+        assert _res_pins(mutant), f"planted resolution-model mistake {mutant} not caught"
+
+
+def test_osem_with_resolution_model():
+    """Count preservation with H: sum_j (s'_j / n_sub) x_new_j equals
+    sum_{e in S} p_e / (p_e + b) with p = A_S H x (as H^T is the adjoint);
+    FWHM 0 gives the plain update."""
+    g, tof, x, xs, xe, tb = _small_lm_problem(n_events=2500, seed=95)
+    rng = np.random.Generator(np.random.PCG64(96))
+    sens = rng.uniform(0.5, 2.0, size=g.shape)
+    b, n_sub, m = 0.4, 4, 2
+    x0 = rng.uniform(0.2, 1.5, size=g.shape)
+    x1 = oracle.lm_osem_subset_update(x0, xs, xe, tb, g, tof, sens, b, m, n_sub, fwhm_mm=4.5)
+    hx = oracle.gauss3d(x0, g, 4.5)
+    p = oracle.fwd(xs[m::n_sub], xe[m::n_sub], hx, g, "tof_lm", tof, tof_bin=tb[m::n_sub])
+    assert float(np.sum(sens / n_sub * x1)) == pytest.approx(float(np.sum(p / (p + b))), rel=1e-12)
+    plain = oracle.lm_osem_subset_update(x0, xs, xe, tb, g, tof, sens, b, m, n_sub)
+    assert np.array_equal(oracle.lm_osem_subset_update(x0, xs, xe, tb, g, tof, sens, b, m, n_sub, fwhm_mm=0.0),
+                          plain)
+    assert np.abs(x1 - plain).max() > 1e-3 * np.abs(plain).max()
