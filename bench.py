@@ -525,6 +525,122 @@ def run_sino(args):
 
 
 # ---------------------------------------------------------------------------
+# sinogram OSEM (34 view subsets, emission + contamination sinograms)
+# ---------------------------------------------------------------------------
+def run_sino_osem(args):
+    """One step = one OSEM iteration over all 34 view subsets of the TOF
+    sinogram (68.1M LORs x 29 bins, 200x200x71), data y ~ Poisson(A x + c)
+    with a uniform contamination c (20 % of the mean projection), all
+    device-resident; with --fwhm > 0 the resolution model wraps A."""
+    from paper_2212_12519_gb300 import build as jbuild, ops, sino_osem, synth
+    jbuild.build()
+    ops.load()
+    dev = torch.device("cuda")
+    g, tof = synth.GEOM_CLINICAL, synth.TOF_CLINICAL
+    spec = synth.SINO_TOF
+    t0 = time.perf_counter()
+    so = sino_osem.SinoOSEM(spec, g, n_sub=34, tof=tof, fwhm_mm=args.fwhm)
+    x_true = synth.ellipsoid_phantom(g, synth.PHANTOM_CLINICAL, 9001, device=dev)
+    so.simulate(x_true, contamination=0.2, seed=9002)
+    setup_s = time.perf_counter() - t0
+    x = torch.empty(g.shape, dtype=torch.float32, device=dev)
+    ops.jp_osem_init(x, sum(so.sens))
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        for m in range(so.n_sub):
+            so.subset_update(x, m)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    launches0 = ops.jp_launch_count()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        for m in range(so.n_sub):
+            so.subset_update(x, m)
+    b.record(stream)
+    torch.cuda.synchronize()
+    launches = ops.jp_launch_count() - launches0
+    clk = clocks.stop()
+    ms = a.elapsed_time(b) / args.steps
+    n_lor = sum(so.n)
+    data_gb = 2 * n_lor * tof.n_bins * 4 / 1e9
+    line = {"metric": "sinogram OSEM iterations/s (34 subsets)", "value": 1e3 / ms, "unit": "iterations/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "sino_osem_tof_68M_x29_200x200x71", "subsets": so.n_sub, "lors": n_lor,
+                       "tof_bins": tof.n_bins, "resolution_fwhm_mm": args.fwhm,
+                       "device_data_gb": data_gb, "l2": "sinograms (>15 GB) larger than L2"},
+            "lor_bins_per_s": n_lor * tof.n_bins / (ms / 1e3), "setup_s": setup_s,
+            "clocks": clk, "gpu_launches": int(launches)}
+    print(json.dumps(line), flush=True)
+    so.close()
+
+
+def run_layout_study(args):
+    """Paper Sec. 3's memory-layout benchmark: forward + back projection of one
+    34-subset sinogram (one view subset of the clinical span-1 sinogram,
+    ~4M LORs, paper: 415 x 8 x 1292) for every sinogram order (PVR, VRP,
+    RVP) x image symmetry axis (0, 1, 2), non-TOF and TOF, through the
+    binned plan and through the one-thread-per-LOR planless kernels in the
+    caller's order.  Prints the time of each and the slowest / fastest
+    ratio per path (the paper's GPU spread: 7.6 non-TOF, 3.6 TOF)."""
+    from paper_2212_12519_gb300 import build as jbuild, ops, synth
+    jbuild.build()
+    ops.load()
+    dev = torch.device("cuda")
+    g0, tof = synth.GEOM_CLINICAL, synth.TOF_CLINICAL
+    spec = synth.SINO_CLINICAL.subset(0, 34)
+    img0 = synth.ellipsoid_phantom(g0, synth.PHANTOM_CLINICAL, 9101, device=dev)
+    rows = []
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    for order in synth.SINO_ORDERS:
+        xs0, xe0 = synth.sinogram_lors(spec, device=dev, order=order)
+        n = xs0.shape[0]
+        for axis in (0, 1, 2):
+            g, xs, xe = synth.symmetry_axis(g0, xs0, xe0, axis)
+            perm = {2: (0, 1, 2), 0: (2, 0, 1), 1: (0, 2, 1)}[axis]
+            img = img0.permute(*perm).contiguous()
+            out = torch.zeros(g.shape, device=dev)
+            plan = ops.jp_plan_create(xs, xe, g)
+            for mode in ("nontof", "tof_sino"):
+                t = tof if mode == "tof_sino" else None
+                y = torch.rand((n, tof.n_bins) if t else (n,), device=dev)
+                if t:
+                    planned = lambda: (ops.jp_fwd_tof_sino(plan, img, t), ops.jp_back_tof_sino(plan, y, t, out))
+                    direct = lambda: (ops.jp_fwd_lors(xs, xe, img, g, "tof_sino", t),
+                                      ops.jp_back_lors(xs, xe, y, g, out, "tof_sino", t))
+                else:
+                    planned = lambda: (ops.jp_fwd(plan, img), ops.jp_back(plan, y, out))
+                    direct = lambda: (ops.jp_fwd_lors(xs, xe, img, g), ops.jp_back_lors(xs, xe, y, g, out))
+                rows.append({"order": order, "symmetry_axis": axis, "mode": mode, "lors": n,
+                             "planned_ms": timed(planned, args.steps), "planless_ms": timed(direct, args.steps)})
+                del y
+            plan.destroy()
+    spread = {}
+    for mode in ("nontof", "tof_sino"):
+        for path in ("planned_ms", "planless_ms"):
+            v = [r[path] for r in rows if r["mode"] == mode]
+            spread[f"{mode}_{path[:-3]}"] = {"min_ms": min(v), "max_ms": max(v), "max_over_min": max(v) / min(v)}
+    print(json.dumps({"metric": "layout study: fwd+back ms per order x symmetry axis",
+                      "config": {"workload": "layout_study_sino_subset", "lors": rows[0]["lors"],
+                                 "image": list(g0.shape), "tof_bins": tof.n_bins},
+                      "spread": spread, "rows": rows}), flush=True)
+
+
+# ---------------------------------------------------------------------------
 # small case for ncu captures: one frame of --events TOF listmode events
 # (launch order: plan [key, scan x3, scatter, flags], then twice
 # [quad build, forward, quad zero, back, fold-back], then a rebind)
@@ -750,7 +866,7 @@ def main():
     ap.add_argument("--serving-rates", default="0.5,1.0,1.5")
     ap.add_argument("--workload", default="tof_lm",
                     choices=["tof_lm", "nontof_lm", "sino_small", "sino_clinical", "tof_sino", "osem",
-                             "profile_case", "profile_osem"])
+                             "sino_osem", "layout_study", "profile_case", "profile_osem"])
     ap.add_argument("--cpu-lors", type=int, default=200_000)
     ap.add_argument("--budget-gb", type=float, default=None)
     ap.add_argument("--no-graphs", action="store_true")
@@ -766,6 +882,10 @@ def main():
         run_profile_osem(args)
     elif args.workload in SINO_WORKLOADS:
         run_sino(args)
+    elif args.workload == "sino_osem":
+        run_sino_osem(args)
+    elif args.workload == "layout_study":
+        run_layout_study(args)
     elif args.workload == "osem":
         from paper_2212_12519_gb300 import build as jbuild, ops
         jbuild.build()

@@ -218,6 +218,20 @@ int jp_osem_update(float* x, const float* bp, const float* sens, float scale, in
                    int32_t n_frames, int64_t img_stride, int64_t s_stride, void* stream);
 
 /*
+ * jp_osem_ratio_sino -- the data term of a sinogram OSEM subset update
+ * (paper Sec. 3: OSEM subset update of a span-1 subset sinogram; Sec. 5:
+ * emission and contamination sinograms), elementwise over n sinogram
+ * entries (LORs x TOF bins, any order shared by the arrays):
+ *     q[i] = p[i] + c[i] > 0 ? y[i] / (p[i] + c[i]) : 0
+ *   p  forward projection A_S x (device float32), may alias q
+ *   y  emission counts (device float32)
+ *   c  additive contamination (device float32), NULL for none
+ * Errors: JP_ERR_ARG (n < 0, NULL p / y / q with n > 0), JP_ERR_ALIGN,
+ * JP_ERR_CUDA.
+ */
+int jp_osem_ratio_sino(const float* proj, const float* y, const float* c, float* q, int64_t n, void* stream);
+
+/*
  * jp_osem_subset_tof_lm -- the projection work of one listmode-OSEM subset
  * update (paper Sec. 2.6 and 3, x <- x / s_sub * A_S^T (1 / (A_S x + b))),
  * fused per event: forward projection of x, ratio 1/(p + b) and back

@@ -12,5 +12,5 @@ closed forms, brute force, invariants and hand-derived values; none is
 from .joseph import (  # noqa: F401
     build, fwd, back, tof_weight, principal_axis, load, MODES,
 )
-from .osem import lm_osem_subset_update, lm_osem, poisson_loglik_grad  # noqa: F401
+from .osem import lm_osem_subset_update, lm_osem, poisson_loglik_grad, sino_osem_subset_update  # noqa: F401
 from .resolution import gauss3d, gauss_taps, sigma_from_fwhm  # noqa: F401

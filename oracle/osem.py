@@ -7,6 +7,10 @@ background b and unit event values,
     x <- x / (s / n_sub) * A_S^T ( 1 / (A_S x + b) ),   x = 0 where s = 0.
 Subset m holds the events e with e mod n_sub == m.
 
+Sinogram OSEM (``sino_osem_subset_update``) uses per-subset sensitivities
+s_S = A_S^T 1 and an additive contamination sinogram c:
+    x <- x / s_S * A_S^T ( y / (A_S x + c) ).
+
 With the image-based resolution model H (``fwhm_mm`` > 0, see
 ``resolution.py``) the update is
     x <- x / (s' / n_sub) * H^T A_S^T ( 1 / (A_S H x + b) )
@@ -52,6 +56,28 @@ def lm_osem(xs, xe, tof_bin, geom, tof, sens, b, n_iter, n_sub, threads=1, x0=No
             x = lm_osem_subset_update(x, xs, xe, tof_bin, geom, tof, sens, b, m, n_sub, threads, fwhm_mm,
                                       truncate)
     return x
+
+
+def sino_osem_subset_update(x, xs, xe, y, c, sens, geom, mode="nontof", tof=None, threads=1):
+    """One sinogram OSEM subset update (paper Sec. 3: an OSEM subset update
+    with 34 subsets of equally spaced views; the emission and contamination
+    sinograms of Sec. 5).  For the subset's LORs (xs, xe), emission counts y
+    and additive contamination c (both [n] non-TOF or [n, n_bins] TOF
+    sinogram) and subset sensitivity sens = A_S^T 1:
+        x <- x / sens * A_S^T ( y / (A_S x + c) ),   x = 0 where sens = 0,
+    reading y / (A_S x + c) as 0 where A_S x + c = 0 (no expected counts)."""
+    p = joseph.fwd(xs, xe, x, geom, mode=mode, tof=tof, threads=threads)
+    den = p + np.asarray(c, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    q = np.zeros_like(den)
+    nz = den > 0
+    q[nz] = y[nz] / den[nz]
+    bp = joseph.back(xs, xe, q, geom, mode=mode, tof=tof, threads=threads)
+    s = np.asarray(sens, dtype=np.float64)
+    out = np.zeros_like(np.asarray(x, dtype=np.float64))
+    pos = s > 0
+    out[pos] = np.asarray(x, dtype=np.float64)[pos] * bp[pos] / s[pos]
+    return out
 
 
 def poisson_loglik_grad(x, xs, xe, tof_bin, geom, tof, w, b, threads=1):

@@ -71,6 +71,7 @@ _SIGS = {
     "jp_back_lors": [P, P, P, P, I64, P, I32, P, P, P, P],
     "jp_osem_ratio": [P, P, P, P, I64, P],
     "jp_osem_update": [P, P, P, F32, I64, I32, I64, I64, P],
+    "jp_osem_ratio_sino": [P, P, P, P, I64, P],
     "jp_sum_f64": [P, I64, P, P],
     "jp_count_samples": [P, I32, P, P, P],
     "jp_osem_subset_tof_lm": [P, I32, I32, P, P, F32, F32, P, P],
@@ -275,14 +276,21 @@ def _img_stride(plan: Plan, img: torch.Tensor, img_stride):
     raise ValueError("image size matches neither one image nor one per frame")
 
 
+def _out_size(out, n, what="out"):
+    if out.numel() < n:
+        raise ValueError(f"{what} holds {out.numel()} elements, the plan needs {n}")
+
+
 def jp_fwd(plan: Plan, img, out=None, img_stride=None, stream=None):
     out = torch.empty(plan.n, dtype=torch.float32, device=img.device) if out is None else out
+    _out_size(out, plan.n)
     _check(load().jp_fwd(plan.handle, _ptr(img, torch.float32, "img"), _img_stride(plan, img, img_stride),
                          _ptr(out, torch.float32, "proj"), _stream(stream)))
     return out
 
 
 def jp_back(plan: Plan, proj, img_accum, img_stride=None, stream=None):
+    _out_size(proj, plan.n, "proj")
     _check(load().jp_back(plan.handle, _ptr(proj, torch.float32, "proj"),
                           _ptr(img_accum, torch.float32, "img_accum"),
                           _img_stride(plan, img_accum, img_stride), _stream(stream)))
@@ -292,6 +300,7 @@ def jp_back(plan: Plan, proj, img_accum, img_stride=None, stream=None):
 def jp_fwd_tof_sino(plan: Plan, img, tof, out=None, img_stride=None, stream=None):
     if out is None:
         out = torch.empty((plan.n, int(tof.n_bins)), dtype=torch.float32, device=img.device)
+    _out_size(out, plan.n * int(tof.n_bins))
     t = tof_params(tof)
     _check(load().jp_fwd_tof_sino(plan.handle, _ptr(img, torch.float32, "img"),
                                   _img_stride(plan, img, img_stride), ctypes.byref(t),
@@ -300,6 +309,7 @@ def jp_fwd_tof_sino(plan: Plan, img, tof, out=None, img_stride=None, stream=None
 
 
 def jp_back_tof_sino(plan: Plan, proj, tof, img_accum, img_stride=None, stream=None):
+    _out_size(proj, plan.n * int(tof.n_bins), "proj")
     t = tof_params(tof)
     _check(load().jp_back_tof_sino(plan.handle, _ptr(proj, torch.float32, "proj"), ctypes.byref(t),
                                    _ptr(img_accum, torch.float32, "img_accum"),
@@ -309,6 +319,7 @@ def jp_back_tof_sino(plan: Plan, proj, tof, img_accum, img_stride=None, stream=N
 
 def jp_fwd_tof_lm(plan: Plan, img, tof, out=None, img_stride=None, stream=None):
     out = torch.empty(plan.n, dtype=torch.float32, device=img.device) if out is None else out
+    _out_size(out, plan.n)
     t = tof_params(tof)
     _check(load().jp_fwd_tof_lm(plan.handle, _ptr(img, torch.float32, "img"),
                                 _img_stride(plan, img, img_stride), ctypes.byref(t),
@@ -317,6 +328,7 @@ def jp_fwd_tof_lm(plan: Plan, img, tof, out=None, img_stride=None, stream=None):
 
 
 def jp_back_tof_lm(plan: Plan, proj, tof, img_accum, img_stride=None, stream=None):
+    _out_size(proj, plan.n, "proj")
     t = tof_params(tof)
     _check(load().jp_back_tof_lm(plan.handle, _ptr(proj, torch.float32, "proj"), ctypes.byref(t),
                                  _ptr(img_accum, torch.float32, "img_accum"),
@@ -384,6 +396,17 @@ def jp_osem_update(x, bp, sens, scale, nvox, n_frames=1, img_stride=None, s_stri
                                  _ptr(sens, torch.float32, "sens"), float(scale), int(nvox), int(n_frames),
                                  int(img_stride), int(s_stride), _stream(stream)))
     return x
+
+
+def jp_osem_ratio_sino(proj, y, c=None, out=None, stream=None):
+    """q = y / (proj + c) (0 where proj + c <= 0); ``out`` may be ``proj``."""
+    out = torch.empty_like(proj) if out is None else out
+    if y.numel() != proj.numel() or out.numel() != proj.numel() or (c is not None and c.numel() != proj.numel()):
+        raise ValueError("proj, y, c and out must have the same number of elements")
+    _check(load().jp_osem_ratio_sino(_ptr(proj, torch.float32, "proj"), _ptr(y, torch.float32, "y"),
+                                     _ptr(c, torch.float32, "c"), _ptr(out, torch.float32, "out"),
+                                     int(proj.numel()), _stream(stream)))
+    return out
 
 
 def jp_osem_subset_tof_lm(plan: Plan, f0: int, f1: int, x, sens, sens_scale: float, b: float, tof,

@@ -117,6 +117,7 @@ class SinoSpec:
     n_views: int
     n_rad: int
     view_step: int = 1  # 2 keeps every 2nd view (TOF sinogram workload)
+    view_start: int = 0
 
     @property
     def n_planes(self) -> int:
@@ -124,7 +125,13 @@ class SinoSpec:
 
     @property
     def views(self) -> np.ndarray:
-        return np.arange(0, self.n_views, self.view_step)
+        return np.arange(self.view_start, self.n_views, self.view_step)
+
+    def subset(self, m: int, n_sub: int) -> "SinoSpec":
+        """Views m, m + n_sub, m + 2 n_sub, ... of this sinogram's views: the
+        equally spaced view subsets of sinogram OSEM (paper Sec. 3)."""
+        return SinoSpec(self.scanner, self.n_views, self.n_rad, self.view_step * n_sub,
+                        self.view_start + m * self.view_step)
 
     @property
     def n_lor(self) -> int:
@@ -139,14 +146,21 @@ SINO_TOF = SinoSpec(SCANNER_CLINICAL, n_views=336, n_rad=313, view_step=2)
 # --------------------------------------------------------------------------
 # sinogram LORs
 # --------------------------------------------------------------------------
-def sinogram_lors(spec: SinoSpec, device="cpu", plane_range: Optional[Tuple[int, int]] = None):
+SINO_ORDERS = ("PVR", "VRP", "RVP")
+
+
+def sinogram_lors(spec: SinoSpec, device="cpu", plane_range: Optional[Tuple[int, int]] = None,
+                  order: str = "PVR"):
     """Crystal-centre endpoints of every LOR of a span-1 sinogram.
 
     Mapping (view v, radial index rho in [-(n_rad-1)/2, (n_rad-1)/2]):
     c1 = (v + floor(rho/2)) mod n_c, c2 = (v - ceil(rho/2) + n_c/2) mod n_c;
-    plane = r1 * n_rings + r2 over all ring pairs.  Flat order is plane-major,
-    then view, then radial (radial fastest).  Returns float32 (xs, xe) [n, 3].
-    ``plane_range`` restricts to planes [p0, p1) (for chunked generation).
+    plane = r1 * n_rings + r2 over all ring pairs.  ``order`` names the flat
+    memory order from the slowest to the fastest axis (paper Sec. 3): "PVR"
+    (default) is plane-major, then view, then radial (radial fastest); "VRP"
+    has the plane fastest and the view slowest; "RVP" the radial slowest and
+    the plane fastest.  Returns float32 (xs, xe) [n, 3].  ``plane_range``
+    restricts to planes [p0, p1) (for chunked generation).
     """
     sc = spec.scanner
     xyz = sc.crystal_xyz(device)  # [R, C, 3] float64
@@ -161,8 +175,26 @@ def sinogram_lors(spec: SinoSpec, device="cpu", plane_range: Optional[Tuple[int,
     r2 = planes - r1 * sc.n_rings
     xs = xyz[r1[:, None, None], c1[None, :, :]]  # [P, V, R, 3]
     xe = xyz[r2[:, None, None], c2[None, :, :]]
+    if order not in SINO_ORDERS:
+        raise ValueError(f"order must be one of {SINO_ORDERS}")
+    perm = {"PVR": (0, 1, 2, 3), "VRP": (1, 2, 0, 3), "RVP": (2, 1, 0, 3)}[order]
+    xs, xe = xs.permute(*perm), xe.permute(*perm)
     return (xs.reshape(-1, 3).to(torch.float32).contiguous(),
             xe.reshape(-1, 3).to(torch.float32).contiguous())
+
+
+def symmetry_axis(geom: "ImageGeom", xs: torch.Tensor, xe: torch.Tensor, axis: int):
+    """Places the scanner's axial direction (z) on image axis ``axis`` (paper
+    Sec. 3, "symmetry axis" 0/1/2; 2 = axial fastest in memory, the default
+    of the other generators): permutes the image geometry and the LOR
+    coordinates alike, so projections equal those of axis 2 up to the voxel
+    permutation.  Returns (geom, xs, xe)."""
+    if axis not in (0, 1, 2):
+        raise ValueError("axis must be 0, 1 or 2")
+    order = {2: (0, 1, 2), 0: (2, 0, 1), 1: (0, 2, 1)}[axis]
+    g = ImageGeom(tuple(geom.shape[i] for i in order), tuple(geom.origin[i] for i in order),
+                  tuple(geom.voxsize[i] for i in order))
+    return g, xs[:, list(order)].contiguous(), xe[:, list(order)].contiguous()
 
 
 # --------------------------------------------------------------------------

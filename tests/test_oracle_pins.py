@@ -647,3 +647,39 @@ def test_osem_with_resolution_model():
     assert np.array_equal(oracle.lm_osem_subset_update(x0, xs, xe, tb, g, tof, sens, b, m, n_sub, fwhm_mm=0.0),
                           plain)
     assert np.abs(x1 - plain).max() > 1e-3 * np.abs(plain).max()
+
+
+# ---------------------------------------------------------------------------
+# sinogram OSEM (paper Sec. 3: subset update with emission and contamination
+# sinograms)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("mode", ["nontof", "tof_sino"])
+def test_sino_osem_fixed_point_and_counts(mode):
+    """(1) Consistent noise-free data y = A_S x + c make x a fixed point
+    (A_S^T 1 / s = 1); (2) sum_j s_j x_new_j = sum_i (A x)_i y_i / ((A x)_i + c_i);
+    (3) equal to the update written with the independent dense tent matrix."""
+    g = G((10, 9, 7), (-4.5, -4.0, -3.3), (1.0, 1.1, 1.2))
+    tof = None if mode == "nontof" else T(bin_width=2.1, sigma=1.7, n_sigmas=3.0, n_bins=9)
+    xs, xe = synth.random_lors(300, g, seed=141)
+    rng = np.random.Generator(np.random.PCG64(142))
+    x = rng.uniform(0.2, 1.5, size=g.shape)
+    p = oracle.fwd(xs, xe, x, g, mode, tof)
+    c = rng.uniform(0.05, 0.3, size=p.shape)
+    sens = oracle.back(xs, xe, np.ones_like(p), g, mode, tof)
+    x_fp = oracle.sino_osem_subset_update(x, xs, xe, p + c, c, sens, g, mode, tof)
+    pos = sens > 0
+    assert np.any(~pos) and np.all(x_fp[~pos] == 0.0)
+    assert np.abs(x_fp[pos] - x[pos]).max() <= 1e-12 * x.max()
+    y = rng.poisson(p + c).astype(np.float64)
+    x1 = oracle.sino_osem_subset_update(x, xs, xe, y, c, sens, g, mode, tof)
+    assert float(np.sum(sens * x1)) == pytest.approx(float(np.sum(p * y / (p + c))), rel=1e-12)
+    A = dense_tent(xs, xe, g, mode, tof)
+    xv = x.reshape(-1)
+    Ax = A @ xv
+    ratio = y.reshape(-1) / (Ax + c.reshape(-1))
+    s_d = A.T @ np.ones(A.shape[0])
+    ref = np.where(s_d > 0, xv * (A.T @ ratio) / np.where(s_d > 0, s_d, 1.0), 0.0)
+    assert np.abs(x1.reshape(-1) - ref).max() <= 1e-11 * np.abs(ref).max()
+    # zero expected counts (A x + c = 0 on a LOR) contribute 0, not NaN
+    x2 = oracle.sino_osem_subset_update(np.zeros(g.shape), xs, xe, y, np.zeros_like(c), sens, g, mode, tof)
+    assert np.all(np.isfinite(x2)) and np.all(x2 == 0.0)
