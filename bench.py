@@ -38,8 +38,8 @@ UNIT = "events/s"
 # (l1tex__t_sectors_pipe_lsu_mem_global_op_red / samples) and DRAM bytes per
 # event (dram__bytes_read.sum + dram__bytes_write.sum over events), scaled to
 # a full launch by the events it processes.
-BACK_SECTORS_PER_SAMPLE = 555_613_207 / 732_745_430
-BACK_DRAM_BYTES_PER_EVENT = (666_795_008 + 77_526_272) / 10_000_000
+BACK_SECTORS_PER_SAMPLE = 534_830_072 / 732_745_430
+BACK_DRAM_BYTES_PER_EVENT = (608_469_248 + 76_418_304) / 10_000_000
 
 
 # ---------------------------------------------------------------------------
@@ -578,6 +578,54 @@ def run_sino_osem(args):
     so.close()
 
 
+def run_lm_osem_iter(args):
+    """Paper Sec. 3/5's LM-OSEM timing: one TOF listmode OSEM iteration
+    (34 subset updates, each with the two resolution-model convolutions)
+    for one frame of 40e6 and of 1.25e6 events on the 200x200x71 grid.
+    The frame's subset plan (binning) is built once before its iterations
+    and timed separately; one iteration is a replayed CUDA graph."""
+    from paper_2212_12519_gb300 import build as jbuild, ops, osem, synth
+    jbuild.build()
+    ops.load()
+    dev = torch.device("cuda")
+    g, tof = synth.GEOM_CLINICAL, synth.TOF_CLINICAL
+    s_raw, _ = osem.sensitivity(g, check=False)
+    sens = osem.resolution_sensitivity(s_raw, g, args.fwhm)
+    ph = synth.ellipsoid_phantom(g, synth.PHANTOM_CLINICAL, 9201, device=dev)
+    b = synth.background_level(ph, tof)
+    out = []
+    for n_ev in (40_000_000, 1_250_000):
+        xs, xe, tb = synth.lm_events(ph, g, synth.SCANNER_CLINICAL, tof, n_ev, seed=9202, device=dev)
+        spec = osem.FrameSpec(xs, xe, tb, g, b, n_iter=1, n_sub=34, fwhm_mm=args.fwhm)
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        fr = osem.LMOSEMFrame(spec, sens, tof)
+        e.record()
+        torch.cuda.synchronize()
+        bin_ms = a.elapsed_time(e)
+        fr.run_graph()  # capture + one iteration
+        for _ in range(args.warmup):
+            fr.run_graph()
+        torch.cuda.synchronize()
+        a.record(fr.stream)
+        for _ in range(args.steps):
+            fr.run_graph()
+        e.record(fr.stream)
+        torch.cuda.synchronize()
+        it_ms = a.elapsed_time(e) / args.steps
+        out.append({"events": n_ev, "subsets": 34, "iteration_ms": it_ms, "plan_ms": bin_ms,
+                    "convolutions_per_iteration": 68 if args.fwhm > 0 else 0,
+                    "paper_gpu_iteration_ms": 600.0 if n_ev == 40_000_000 else 57.0})
+        fr.release()
+        del fr, xs, xe, tb, spec
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": "TOF LM-OSEM ms per iteration (34 subsets)",
+                      "config": {"workload": "lm_osem_iteration_200x200x71", "resolution_fwhm_mm": args.fwhm,
+                                 "steps": args.steps, "warmup": args.warmup},
+                      "rows": out}), flush=True)
+
+
 def run_layout_study(args):
     """Paper Sec. 3's memory-layout benchmark: forward + back projection of one
     34-subset sinogram (one view subset of the clinical span-1 sinogram,
@@ -646,8 +694,9 @@ def run_layout_study(args):
 # [quad build, forward, quad zero, back, fold-back], then a rebind)
 # ---------------------------------------------------------------------------
 def run_profile_osem(args):
-    """One served frame (--events events, 200x200x71), 3 iterations x 8
-    subsets through direct launches, for the ncu launch list."""
+    """One frame (--events events, 200x200x71), one iteration of 34 subsets
+    (with the --fwhm resolution model) through direct launches, for the ncu
+    launch list."""
     from paper_2212_12519_gb300 import build as jbuild, ops, osem, synth
     jbuild.build()
     ops.load()
@@ -656,7 +705,7 @@ def run_profile_osem(args):
     ph = synth.ellipsoid_phantom(g, synth.PHANTOM_CLINICAL, 5010, device=dev)
     xs, xe, tb = synth.lm_events(ph, g, synth.SCANNER_CLINICAL, tof, args.events, seed=5011, device=dev)
     sens = torch.ones(g.shape, device=dev)
-    spec = osem.FrameSpec(xs, xe, tb, g, synth.background_level(ph, tof), fwhm_mm=args.fwhm)
+    spec = osem.FrameSpec(xs, xe, tb, g, synth.background_level(ph, tof), n_iter=1, n_sub=34, fwhm_mm=args.fwhm)
     fr = osem.LMOSEMFrame(spec, sens, tof)
     fr.run()
     torch.cuda.synchronize()
@@ -866,7 +915,7 @@ def main():
     ap.add_argument("--serving-rates", default="0.5,1.0,1.5")
     ap.add_argument("--workload", default="tof_lm",
                     choices=["tof_lm", "nontof_lm", "sino_small", "sino_clinical", "tof_sino", "osem",
-                             "sino_osem", "layout_study", "profile_case", "profile_osem"])
+                             "sino_osem", "layout_study", "lm_osem_iter", "profile_case", "profile_osem"])
     ap.add_argument("--cpu-lors", type=int, default=200_000)
     ap.add_argument("--budget-gb", type=float, default=None)
     ap.add_argument("--no-graphs", action="store_true")
@@ -886,6 +935,8 @@ def main():
         run_sino_osem(args)
     elif args.workload == "layout_study":
         run_layout_study(args)
+    elif args.workload == "lm_osem_iter":
+        run_lm_osem_iter(args)
     elif args.workload == "osem":
         from paper_2212_12519_gb300 import build as jbuild, ops
         jbuild.build()

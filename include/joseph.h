@@ -293,20 +293,35 @@ int jp_gauss3d(const float* img, float* out, float* work, int32_t n_images, cons
                const jp_resolution* r, void* stream);
 
 /*
- * jp_osem_subset_tof_lm_res -- listmode OSEM subset update with the
- * resolution model (paper Sec. 3):
+ * jp_osem_subset_tof_lm_ex -- listmode OSEM subset update, general form:
  *   x[j] <- sens[j] > 0 ? x[j] * (H^T A_S^T (1 / (A_S H x + b)))[j] / (sens[j] * sens_scale) : 0
- * where sens is the caller's H^T A^T 1.  Plan, frame range and TOF rules as
- * jp_osem_subset_tof_lm; b_dev non-NULL reads b from device memory and the
- * event range from the plan's device offsets (CUDA-graph capturable, as
- * jp_osem_subset_tof_lm_dev), otherwise the scalar b is used.
+ * with the resolution model H of r (paper Sec. 3), or H = identity when r
+ * is NULL; sens is then the caller's H^T A^T 1.  Plan, frame range and TOF
+ * rules as jp_osem_subset_tof_lm; b_dev non-NULL reads b from device memory
+ * and the event range from the plan's device offsets (CUDA-graph
+ * capturable, as jp_osem_subset_tof_lm_dev), otherwise the scalar b is used.
+ *   path  JP_OSEM_PATH_QUADS: the projections go through the plan's
+ *         zero-padded quad images (one 16-byte access per sample; an
+ *         image-sized build, clear and fold per call);
+ *         JP_OSEM_PATH_DIRECT: forward from the image, back projection by
+ *         scalar atomics into an image (no quad traffic; cheaper for
+ *         subsets of fewer than about nvox / 32 events, measured on GB300
+ *         for 128x128x71 and 200x200x71 images);
+ *         JP_OSEM_PATH_AUTO: DIRECT when b_dev is NULL and the subset holds
+ *         fewer than nvox / JP_OSEM_DIRECT_VOXELS_PER_EVENT events, else
+ *         QUADS.  All paths compute the same update.
  *   work  device float32 scratch of 2 * nvox, caller-owned, disjoint from x
- *         and sens.
- * Errors: those of jp_osem_subset_tof_lm and jp_gauss3d.
+ *         and sens; required when r is non-NULL, else unused (may be NULL).
+ * Errors: those of jp_osem_subset_tof_lm and jp_gauss3d; JP_ERR_ARG for an
+ * unknown path.
  */
-int jp_osem_subset_tof_lm_res(jp_plan p, int32_t f0, int32_t f1, float* x, const float* sens,
-                              float sens_scale, float b, const float* b_dev, const jp_tof* t,
-                              const jp_resolution* r, float* work, void* stream);
+#define JP_OSEM_PATH_AUTO 0
+#define JP_OSEM_PATH_QUADS 1
+#define JP_OSEM_PATH_DIRECT 2
+#define JP_OSEM_DIRECT_VOXELS_PER_EVENT 32
+int jp_osem_subset_tof_lm_ex(jp_plan p, int32_t f0, int32_t f1, float* x, const float* sens,
+                             float sens_scale, float b, const float* b_dev, const jp_tof* t,
+                             const jp_resolution* r, int32_t path, float* work, void* stream);
 
 /*
  * Listmode Poisson log-likelihood of a forward projection p (the training

@@ -325,4 +325,5 @@ struct jp_plan_s {
   int32_t quad_slots;     // frames with their own image, or 2 (image + back projection) when interleaved
   int32_t* axis_used;     // [frame_capacity * 3]: frame f has LORs with principal axis a
   uint32_t* work_counter; // chunk counter of the persistent projection kernels
+  float* fold_img;        // [nvox] folded back projection of an OSEM subset (interleaved plans only)
 };

@@ -351,6 +351,7 @@ void free_plan(jp_plan p) {
   cudaFree(p->quads);
   cudaFree(p->axis_used);
   cudaFree(p->work_counter);
+  cudaFree(p->fold_img);
   delete p;
 }
 
@@ -438,6 +439,8 @@ extern "C" int jp_plan_create_batch(jp_plan* out, const float* xs, const float* 
   if (e == cudaSuccess) e = cudaMalloc(&p->quads, sizeof(float4) * (size_t)p->ql.slot * (size_t)p->quad_slots);
   if (e == cudaSuccess) e = cudaMalloc(&p->axis_used, sizeof(int32_t) * 3 * (size_t)n_frames);
   if (e == cudaSuccess) e = cudaMalloc(&p->work_counter, 256);
+  if (e == cudaSuccess && interleaved)
+    e = cudaMalloc(&p->fold_img, sizeof(float) * (size_t)g->n[0] * g->n[1] * g->n[2]);
   if (e != cudaSuccess) {
     cudaGetLastError();
     free_plan(p);

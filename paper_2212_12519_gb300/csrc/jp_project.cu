@@ -493,7 +493,14 @@ __global__ void __launch_bounds__(kMaxBlock) group_kernel(const ProjParams p) {
 // p.quads), ratio 1 / (p + b), back projection of the ratio into p.quads_bp.
 // G lanes per event as in group_kernel; both quad sets are plane-fastest.
 // ---------------------------------------------------------------------------
-template <bool LUT, int G>
+// DIRECT = false: forward from the plane-fastest quads of p.img_in (p.quads),
+// back projection into the back-projection quads (p.quads_bp), one 16-byte
+// load / reduction per sample.  DIRECT = true: forward from the image
+// p.img_in itself (4 bounded loads per sample) and back projection with 4
+// scalar atomics per sample into the image p.img_out (zeroed by the caller):
+// no image-sized quad build, clear and fold, which is the cheaper trade for
+// small subsets.  Both compute the same samples with the same arithmetic.
+template <bool LUT, int G, bool DIRECT>
 __global__ void __launch_bounds__(kMaxBlock) osem_kernel(const ProjParams p) {
   constexpr int E = 32 / G;
   extern __shared__ float4 smem4[];
@@ -508,16 +515,24 @@ __global__ void __launch_bounds__(kMaxBlock) osem_kernel(const ProjParams p) {
   const int grp = lane / G, gl = lane - grp * G;
   const int64_t start = __ldg(p.frame_off + p.f0), end = __ldg(p.frame_off + p.f1);
   const float bg = p.bg_ptr ? __ldg(p.bg_ptr) : p.bg;
+  // A warp takes chunks of cp passes x E events.  A small subset gets
+  // cp < G, so that its events spread over every warp of the grid instead
+  // of queueing G passes deep on a few warps (the passes of a chunk run one
+  // after the other); large subsets use full 32-event chunks.
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t per = (end - start + warps * E - 1) / (warps * E);
+  const int cp = (int)(per < 1 ? 1 : (per > G ? G : per));
+  const int chunk_ev = cp * E;
   for (;;) {
     unsigned int chunk = 0;
     if (lane == 0) chunk = atomicAdd(p.counter, 1u);
-    const int64_t base = start + (int64_t)__shfl_sync(0xffffffffu, chunk, 0) * 32;
+    const int64_t base = start + (int64_t)__shfl_sync(0xffffffffu, chunk, 0) * chunk_ev;
     if (base >= end) break;
     const int64_t i = base + lane;
     Ray r;
     r.k0 = 1; r.k1 = 0;
     float d0 = 0.f;
-    if (i < end) {
+    if (lane < chunk_ev && i < end) {
       const float4 A = __ldcs(p.lor + 2 * i);
       const float4 B = __ldcs(p.lor + 2 * i + 1);
       const float xs[3] = {A.x, A.y, A.z};
@@ -538,7 +553,7 @@ __global__ void __launch_bounds__(kMaxBlock) osem_kernel(const ProjParams p) {
       r.a = 0; r.uc = r.du = r.wc = r.dw = r.tc = r.dt = r.w0 = 0.f;
     }
 #pragma unroll 1
-    for (int pass = 0; pass < G; ++pass) {
+    for (int pass = 0; pass < cp; ++pass) {
       const int src = pass * E + grp;
       const int k0 = __shfl_sync(0xffffffffu, r.k0, src);
       const int k1 = __shfl_sync(0xffffffffu, r.k1, src);
@@ -558,6 +573,10 @@ __global__ void __launch_bounds__(kMaxBlock) osem_kernel(const ProjParams p) {
       const float kc = 0.5f * (float)(na - 1);
       const float ub = (float)nb, wb = (float)nc;
       const int64_t qoff = sel3(a, p.ql.base[0], p.ql.base[1], p.ql.base[2]);
+      // image strides along the plane axis a and the in-plane axes b, c
+      const int sa = sel3(a, p.g.stride[0], p.g.stride[1], p.g.stride[2]);
+      const int sb = (a == 0) ? p.g.stride[1] : p.g.stride[0];
+      const int sc = (a == 2) ? p.g.stride[1] : p.g.stride[2];
       // forward
       float sum = 0.f;
       for (int k = k0 + gl; k <= k1; k += G) {
@@ -566,7 +585,19 @@ __global__ void __launch_bounds__(kMaxBlock) osem_kernel(const ProjParams p) {
         const float w = fminf(fmaxf(fmaf(kk, dw, wc), -1.f), wb);
         const float fu = floorf(u), fw = floorf(w);
         const float al = u - fu, be = w - fw;
-        const float4 v = __ldg(p.quads + qoff + (((int)fu + 1) * nc2 + ((int)fw + 1)) * nap + k);
+        float4 v;
+        if (DIRECT) {
+          const int i = (int)fu, j = (int)fw;
+          const bool i0 = (unsigned)i < (unsigned)nb, i1 = (unsigned)(i + 1) < (unsigned)nb;
+          const bool j0 = (unsigned)j < (unsigned)nc, j1 = (unsigned)(j + 1) < (unsigned)nc;
+          const int64_t idx = (int64_t)k * sa + (int64_t)i * sb + (int64_t)j * sc;
+          v.x = (i0 && j0) ? __ldg(p.img_in + idx) : 0.f;
+          v.y = (i1 && j0) ? __ldg(p.img_in + idx + sb) : 0.f;
+          v.z = (i0 && j1) ? __ldg(p.img_in + idx + sc) : 0.f;
+          v.w = (i1 && j1) ? __ldg(p.img_in + idx + sb + sc) : 0.f;
+        } else {
+          v = __ldg(p.quads + qoff + (((int)fu + 1) * nc2 + ((int)fw + 1)) * nap + k);
+        }
         const float top = fmaf(be, v.z - v.x, v.x);
         const float bot = fmaf(be, v.w - v.y, v.y);
         sum = fmaf(tof_weight<LUT>(lut, fmaf(kk, ddt, dd0), T, inv_h), fmaf(al, bot - top, top), sum);
@@ -583,8 +614,19 @@ __global__ void __launch_bounds__(kMaxBlock) osem_kernel(const ProjParams p) {
         const float al = u - fu, be = w - fw;
         const float coef = coef0 * tof_weight<LUT>(lut, fmaf(kk, ddt, dd0), T, inv_h);
         const float ca = (1.f - al) * coef, cb = al * coef;
-        atomicAdd(p.quads_bp + qoff + (((int)fu + 1) * nc2 + ((int)fw + 1)) * nap + k,
-                  make_float4(ca * (1.f - be), cb * (1.f - be), ca * be, cb * be));
+        if (DIRECT) {
+          const int i = (int)fu, j = (int)fw;
+          const bool i0 = (unsigned)i < (unsigned)nb, i1 = (unsigned)(i + 1) < (unsigned)nb;
+          const bool j0 = (unsigned)j < (unsigned)nc, j1 = (unsigned)(j + 1) < (unsigned)nc;
+          const int64_t idx = (int64_t)k * sa + (int64_t)i * sb + (int64_t)j * sc;
+          if (i0 && j0) atomicAdd(p.img_out + idx, ca * (1.f - be));
+          if (i1 && j0) atomicAdd(p.img_out + idx + sb, cb * (1.f - be));
+          if (i0 && j1) atomicAdd(p.img_out + idx + sc, ca * be);
+          if (i1 && j1) atomicAdd(p.img_out + idx + sb + sc, cb * be);
+        } else {
+          atomicAdd(p.quads_bp + qoff + (((int)fu + 1) * nc2 + ((int)fw + 1)) * nap + k,
+                    make_float4(ca * (1.f - be), cb * (1.f - be), ca * be, cb * be));
+        }
       }
     }
   }
@@ -681,6 +723,141 @@ __global__ void quad_build_kernel(const ProjParams p) {
     v.z = (i0 && j1) ? __ldg(im + base + sc) : 0.f;
     v.w = (i1 && j1) ? __ldg(im + base + sb + sc) : 0.f;
     Q[e] = v;
+  }
+}
+
+// Plane-fastest quads (p.kfast) of axes 0 and 1 are stored with k fastest
+// while the image has its axis 2 (the quads' j) fastest, so a thread per
+// quad entry reads the image with a large stride and a thread per voxel
+// reads the quads with one.  The tiled kernels below stage a kT x kT
+// (k, j) tile of one quad row through shared memory instead: both global
+// sides are then read and written in their own fastest order.  (Axis 2 has
+// k fastest on both sides; the same kernels handle it with k-fastest loops.)
+constexpr int kT = 32;
+
+// Builds plane-fastest quads from p.img_in: grid x over (j, k) tiles, y over
+// quad rows i = -1 .. nb, z over (slot, axis); sized for the largest axis.
+__global__ void __launch_bounds__(256) quad_build_tile_kernel(const ProjParams p) {
+  if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 && p.counter) *p.counter = 0u;
+  const int slot = blockIdx.z / 3, a = blockIdx.z - 3 * (blockIdx.z / 3);
+  if (!slot_axis_used(p.axis_used, slot, a, p.shared, p.n_frames)) return;
+  const int b = (a == 0) ? 1 : 0, c = (a == 2) ? 1 : 2;
+  const DevGeom& g = p.g;
+  const int na = sel3(a, g.n[0], g.n[1], g.n[2]);
+  const int nb = sel3(b, g.n[0], g.n[1], g.n[2]), nc = sel3(c, g.n[0], g.n[1], g.n[2]);
+  const int sa = sel3(a, g.stride[0], g.stride[1], g.stride[2]);
+  const int sb = sel3(b, g.stride[0], g.stride[1], g.stride[2]);
+  const int sc = sel3(c, g.stride[0], g.stride[1], g.stride[2]);
+  const int nap = sel3(a, p.ql.nap[0], p.ql.nap[1], p.ql.nap[2]);
+  const int nc2 = nc + 2;
+  const int i = (int)blockIdx.y - 1;  // quad base row
+  if (i > nb) return;
+  const int ktiles = (nap + kT - 1) / kT, jtiles = (nc2 + kT - 1) / kT;
+  if ((int)blockIdx.x >= ktiles * jtiles) return;
+  const int jt = blockIdx.x / ktiles, kt = blockIdx.x - jt * ktiles;
+  const int j0 = jt * kT - 1, k0 = kt * kT;
+  __shared__ float s[2][kT][kT + 1];  // [row i + r][k - k0][j - j0], j - j0 in 0..kT
+  const float* __restrict__ im = p.img_in + (int64_t)slot * p.img_stride;
+  for (int t = threadIdx.x; t < 2 * kT * (kT + 1); t += blockDim.x) {
+    int r, kk, jj;
+    if (a == 2) {  // image fastest along k
+      kk = t % kT;
+      const int u = t / kT;
+      jj = u % (kT + 1);
+      r = u / (kT + 1);
+    } else {       // image fastest along j
+      jj = t % (kT + 1);
+      const int u = t / (kT + 1);
+      kk = u % kT;
+      r = u / kT;
+    }
+    const int k = k0 + kk, ii = i + r, j = j0 + jj;
+    float v = 0.f;
+    if (k < na && (unsigned)ii < (unsigned)nb && (unsigned)j < (unsigned)nc)
+      v = __ldg(im + (int64_t)k * sa + (int64_t)ii * sb + (int64_t)j * sc);
+    s[r][kk][jj] = v;
+  }
+  __syncthreads();
+  float4* Q = p.quads + (int64_t)slot * p.ql.slot + sel3(a, p.ql.base[0], p.ql.base[1], p.ql.base[2]);
+  for (int t = threadIdx.x; t < kT * kT; t += blockDim.x) {
+    const int kk = t % kT, jj = t / kT;
+    const int k = k0 + kk, j = j0 + jj;
+    if (k >= nap || j > nc) continue;
+    Q[((int64_t)(i + 1) * nc2 + (j + 1)) * nap + k] =
+        make_float4(s[0][kk][jj], s[1][kk][jj], s[0][kk][jj + 1], s[1][kk][jj + 1]);
+  }
+}
+
+// out[slot] (=|+=) the fold of axis a's plane-fastest quads (base quads_base,
+// slot stride ql.slot): voxel (k, I, J) of the axis collects the four quad
+// slots that hold it.  ADD = false writes every voxel (0 where the axis is
+// unused), so a sequence "axis 0 write, axes 1 and 2 add" needs no zeroing.
+// Grid x over (J, k) tiles, y over I = 0 .. nb - 1, z over slots.
+template <bool ADD>
+__global__ void __launch_bounds__(256) quad_fold_tile_kernel(const ProjParams p, const float4* __restrict__ quads_base,
+                                                             float* __restrict__ out_base, int a) {
+  const int slot = blockIdx.z;
+  const bool used = slot_axis_used(p.axis_used, slot, a, p.shared, p.n_frames);
+  if (ADD && !used) return;
+  const int b = (a == 0) ? 1 : 0, c = (a == 2) ? 1 : 2;
+  const DevGeom& g = p.g;
+  const int na = sel3(a, g.n[0], g.n[1], g.n[2]);
+  const int nc = sel3(c, g.n[0], g.n[1], g.n[2]);
+  const int sa = sel3(a, g.stride[0], g.stride[1], g.stride[2]);
+  const int sb = sel3(b, g.stride[0], g.stride[1], g.stride[2]);
+  const int sc = sel3(c, g.stride[0], g.stride[1], g.stride[2]);
+  const int nap = sel3(a, p.ql.nap[0], p.ql.nap[1], p.ql.nap[2]);
+  const int nc2 = nc + 2;
+  const int I = blockIdx.y;
+  const int ktiles = (na + kT - 1) / kT;
+  const int jt = blockIdx.x / ktiles, kt = blockIdx.x - jt * ktiles;
+  const int J0 = jt * kT, k0 = kt * kT;
+  // component planes: 0 = x and 1 = z of padded row I + 1, 2 = y and 3 = w
+  // of padded row I; [plane][padded col - J0][k - k0]
+  __shared__ float s[4][kT + 1][kT + 1];
+  if (used) {
+    const float4* Q = quads_base + (int64_t)slot * p.ql.slot + sel3(a, p.ql.base[0], p.ql.base[1], p.ql.base[2]);
+    for (int t = threadIdx.x; t < 2 * (kT + 1) * kT; t += blockDim.x) {
+      const int kk = t % kT;
+      const int u = t / kT;
+      const int pjj = u % (kT + 1), r = u / (kT + 1);
+      const int k = k0 + kk, pj = J0 + pjj;
+      float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (k < na && pj <= nc + 1) q = Q[((int64_t)(I + r) * nc2 + pj) * nap + k];
+      if (r) {
+        s[0][pjj][kk] = q.x;
+        s[1][pjj][kk] = q.z;
+      } else {
+        s[2][pjj][kk] = q.y;
+        s[3][pjj][kk] = q.w;
+      }
+    }
+  }
+  __syncthreads();
+  float* out = out_base + (int64_t)slot * p.img_stride;
+  for (int t = threadIdx.x; t < kT * kT; t += blockDim.x) {
+    int kk, jj;
+    if (a == 2) {
+      kk = t % kT;
+      jj = t / kT;
+    } else {
+      jj = t % kT;
+      kk = t / kT;
+    }
+    const int k = k0 + kk, J = J0 + jj;
+    if (k >= na || J >= nc) continue;
+    const float val = used ? s[0][jj + 1][kk] + s[2][jj + 1][kk] + s[1][jj][kk] + s[3][jj][kk] : 0.f;
+    const int64_t v = (int64_t)k * sa + (int64_t)I * sb + (int64_t)J * sc;
+    out[v] = ADD ? out[v] + val : val;
+  }
+}
+
+// x[v] <- s[v] * scale > 0 ? x[v] * bp[v] / (s[v] * scale) : 0
+__global__ void img_update_kernel(float* __restrict__ x, const float* __restrict__ bp, const float* __restrict__ sens,
+                                  float scale, int64_t nvox) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvox; v += (int64_t)gridDim.x * blockDim.x) {
+    const float sv = __ldg(sens + v) * scale;
+    x[v] = sv > 0.f ? x[v] * __ldg(bp + v) / sv : 0.f;
   }
 }
 
@@ -949,6 +1126,57 @@ int aux_grid(int64_t work, int block) {
   return (int)(g < 1 ? 1 : g);
 }
 
+// per-axis extents (n_a, n_b, n_c) of the quad images
+void axis_dims(const DevGeom& g, int a, int* na, int* nb, int* nc) {
+  *na = g.n[a];
+  *nb = (a == 0) ? g.n[1] : g.n[0];
+  *nc = (a == 2) ? g.n[1] : g.n[2];
+}
+
+// the tiled kernels index rows through gridDim.y
+bool tiles_fit(const DevGeom& g) {
+  for (int a = 0; a < 3; ++a) {
+    int na, nb, nc;
+    axis_dims(g, a, &na, &nb, &nc);
+    if (nb + 2 > 65535) return false;
+  }
+  return true;
+}
+
+// plane-fastest quads of every (slot, axis) from p.img_in
+int launch_quad_build_tile(const ProjParams& p, int slots, cudaStream_t st) {
+  int gx = 1, gy = 1;
+  for (int a = 0; a < 3; ++a) {
+    int na, nb, nc;
+    axis_dims(p.g, a, &na, &nb, &nc);
+    const int nap = p.ql.nap[a];
+    gx = std::max(gx, ((nap + kT - 1) / kT) * ((nc + 2 + kT - 1) / kT));
+    gy = std::max(gy, nb + 2);
+  }
+  quad_build_tile_kernel<<<dim3(gx, gy, slots * 3), 256, 0, st>>>(p);
+  count_launch();
+  JP_TRY_CUDA(cudaGetLastError());
+  return JP_OK;
+}
+
+// out[slot] (+)= fold of the plane-fastest quads at `quads` over all axes;
+// add_all = false overwrites out with the fold (axis 0 writes, 1 and 2 add)
+int launch_quad_fold_tile(const ProjParams& p, const float4* quads, float* out, int slots, bool add_all,
+                          cudaStream_t st) {
+  for (int a = 0; a < 3; ++a) {
+    int na, nb, nc;
+    axis_dims(p.g, a, &na, &nb, &nc);
+    const dim3 grid(((nc + kT - 1) / kT) * ((na + kT - 1) / kT), nb, slots);
+    if (a == 0 && !add_all)
+      quad_fold_tile_kernel<false><<<grid, 256, 0, st>>>(p, quads, out, a);
+    else
+      quad_fold_tile_kernel<true><<<grid, 256, 0, st>>>(p, quads, out, a);
+    count_launch();
+    JP_TRY_CUDA(cudaGetLastError());
+  }
+  return JP_OK;
+}
+
 int planned(jp_plan pl, int mode, bool back, const float* in, float* out, int64_t img_stride,
             const jp_tof* t, void* stream) {
   clear_error();
@@ -997,13 +1225,18 @@ int planned(jp_plan pl, int mode, bool back, const float* in, float* out, int64_
   if (mode == 1 && !back) lpw = 32;
   p.kfast = (lpw == 32) ? 0 : 1;
   dim3 qgrid(aux_grid(max_quad, 256), slots * 3);
-  if (!back) {
-    quad_build_kernel<<<qgrid, 256, 0, st>>>(p);
+  const bool tiled = p.kfast && tiles_fit(p.g);
+  if (!back && tiled) {
+    rc = launch_quad_build_tile(p, slots, st);
+    if (rc) return rc;
   } else {
-    quad_zero_kernel<<<qgrid, 256, 0, st>>>(p);
+    if (!back)
+      quad_build_kernel<<<qgrid, 256, 0, st>>>(p);
+    else
+      quad_zero_kernel<<<qgrid, 256, 0, st>>>(p);
+    count_launch();
+    JP_TRY_CUDA(cudaGetLastError());
   }
-  count_launch();
-  JP_TRY_CUDA(cudaGetLastError());
   switch (mode * 4 + (back ? 2 : 0) + (lut ? 1 : 0)) {
     case 0: rc = launch_group_lpw<0, false, false>(p, block, lpw, st); break;
     case 2: rc = launch_group_lpw<0, true, false>(p, block, lpw, st); break;
@@ -1018,6 +1251,7 @@ int planned(jp_plan pl, int mode, bool back, const float* in, float* out, int64_
     default: return fail(JP_ERR_ARG, "bad mode");
   }
   if (rc) return rc;
+  if (back && tiled) return launch_quad_fold_tile(p, p.quads, p.img_out, slots, true, st);
   if (back) {
     const int64_t nvox = (int64_t)p.g.n[0] * p.g.n[1] * p.g.n[2];
     dim3 rgrid(aux_grid(nvox, 256), slots);
@@ -1128,9 +1362,15 @@ namespace jp {
 namespace {
 // One listmode-OSEM subset update; with res non-NULL the resolution model H
 // wraps the projections (x -> H x before the forward projection, H^T on the
-// back projection before the update), using work[0 .. 2 nvox).
+// back projection before the update), using work[0 .. 2 nvox).  path: one of
+// JP_OSEM_PATH_* (AUTO takes the direct path for subsets of fewer than
+// nvox / JP_OSEM_DIRECT_VOXELS_PER_EVENT events when their count is known on
+// the host: below that the quad path's image-sized build, clear and fold
+// cost more than the direct path's scalar atomics).
+
 int osem_subset(jp_plan pl, int32_t f0, int32_t f1, float* x, const float* sens, float sens_scale, float b,
-                const float* b_dev, const jp_tof* t, const jp_resolution* res, float* work, void* stream) {
+                const float* b_dev, const jp_tof* t, const jp_resolution* res, int32_t path, float* work,
+                void* stream) {
   clear_error();
   if (!pl) return fail(JP_ERR_ARG, "plan is NULL");
   if (!(pl->opts.flags & JP_PLAN_INTERLEAVED)) return fail(JP_ERR_STATE, "OSEM subsets need a JP_PLAN_INTERLEAVED plan");
@@ -1140,6 +1380,8 @@ int osem_subset(jp_plan pl, int32_t f0, int32_t f1, float* x, const float* sens,
   if (!aligned(x, 4) || !aligned(sens, 4) || !aligned(b_dev, 4)) return fail(JP_ERR_ALIGN, "arrays must be 4-byte aligned");
   if (!(sens_scale > 0.f) || !isfinite(sens_scale)) return fail(JP_ERR_ARG, "sens_scale must be finite and > 0");
   if (!b_dev && (!(b >= 0.f) || !isfinite(b))) return fail(JP_ERR_ARG, "b must be finite and >= 0");
+  if (path != JP_OSEM_PATH_AUTO && path != JP_OSEM_PATH_QUADS && path != JP_OSEM_PATH_DIRECT)
+    return fail(JP_ERR_ARG, "path must be JP_OSEM_PATH_AUTO, _QUADS or _DIRECT");
   ProjParams p;
   std::memset(&p, 0, sizeof(p));
   int rc = make_geom(&pl->g, &p.g);
@@ -1162,6 +1404,14 @@ int osem_subset(jp_plan pl, int32_t f0, int32_t f1, float* x, const float* sens,
     wy = work;
     wt = work + nvox;
   }
+  // the event count is known only on the device when b is read there (a
+  // captured graph serves every frame bound later): size the grid by the
+  // host-side count when it is current, else fill the GPU
+  const int64_t host_n = b_dev ? pl->capacity : pl->frame_off_host[f1] - pl->frame_off_host[f0];
+  const bool tiled = tiles_fit(p.g);
+  bool direct = path == JP_OSEM_PATH_DIRECT;
+  if (path == JP_OSEM_PATH_AUTO) direct = !b_dev && host_n < nvox / JP_OSEM_DIRECT_VOXELS_PER_EVENT;
+  if (direct && !pl->fold_img) return fail(JP_ERR_STATE, "plan has no fold image");
   p.lor = pl->lor;
   p.perm = pl->perm;
   p.frame_off = pl->frame_off_dev;
@@ -1189,50 +1439,86 @@ int osem_subset(jp_plan pl, int32_t f0, int32_t f1, float* x, const float* sens,
   p.sens_scale = sens_scale;
   p.counter = pl->work_counter;
   p.perm_in_rec = pl->has_delta ? 0 : 1;
+  // back-projection image of the direct path (and of the quads path's fold)
+  float* bp_img = res ? wt : pl->fold_img;
   const int64_t max_quad = std::max(std::max(p.ql.size[0], p.ql.size[1]), p.ql.size[2]);
   dim3 qgrid(aux_grid(max_quad, 256), 3);
-  quad_build_kernel<<<qgrid, 256, 0, st>>>(p);
-  count_launch();
-  {
+  if (direct) {
+    p.img_out = bp_img;
+    JP_TRY_CUDA(cudaMemsetAsync(bp_img, 0, sizeof(float) * nvox, st));
+    JP_TRY_CUDA(cudaMemsetAsync(p.counter, 0, sizeof(uint32_t), st));
+  } else {
+    if (tiled) {
+      rc = launch_quad_build_tile(p, 1, st);
+      if (rc) return rc;
+    } else {
+      quad_build_kernel<<<qgrid, 256, 0, st>>>(p);
+      count_launch();
+    }
     ProjParams z = p;
     z.quads = p.quads_bp;
     quad_zero_kernel<<<qgrid, 256, 0, st>>>(z);
     count_launch();
+    JP_TRY_CUDA(cudaGetLastError());
   }
-  JP_TRY_CUDA(cudaGetLastError());
   if (pl->capacity > 0) {
     const bool lut = !(pl->opts.flags & JP_PLAN_TOF_EXACT);
     int lpw = pl->opts.lors_per_warp;
     if (lpw != 1 && lpw != 2) lpw = 4;
     const int block = std::min(pl->opts.block, kMaxBlock);
     const size_t smem = lut ? kLut * sizeof(float2) : 0;
-    // the event count is known only on the device: size the grid by the
-    // host-side count when it is current, else fill the GPU
-    const int64_t host_n = b_dev ? pl->capacity : pl->frame_off_host[f1] - pl->frame_off_host[f0];
+    // events one warp pass handles: 32 / G
+    const int64_t ev_per_block = (int64_t)(lpw == 1 ? 1 : (lpw == 2 ? 2 : 4)) * (block / 32);
     auto pick = [&](auto kern) -> int {
       int per_sm = 0;
       JP_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem));
       int64_t grid = (int64_t)sm_count() * (per_sm < 1 ? 1 : per_sm);
-      const int64_t need = (host_n + block - 1) / block;
+      const int64_t need = (host_n + ev_per_block - 1) / ev_per_block;
       if (grid > need) grid = need;
       kern<<<(unsigned)(grid < 1 ? 1 : grid), block, smem, st>>>(p);
       count_launch();
       JP_TRY_CUDA(cudaGetLastError());
       return JP_OK;
     };
-    if (lut) rc = (lpw == 1) ? pick(osem_kernel<true, 32>) : (lpw == 2 ? pick(osem_kernel<true, 16>) : pick(osem_kernel<true, 8>));
-    else rc = (lpw == 1) ? pick(osem_kernel<false, 32>) : (lpw == 2 ? pick(osem_kernel<false, 16>) : pick(osem_kernel<false, 8>));
+    const int sel = (lut ? 6 : 0) + (direct ? 3 : 0) + (lpw == 1 ? 0 : (lpw == 2 ? 1 : 2));
+    switch (sel) {
+      case 0: rc = pick(osem_kernel<false, 32, false>); break;
+      case 1: rc = pick(osem_kernel<false, 16, false>); break;
+      case 2: rc = pick(osem_kernel<false, 8, false>); break;
+      case 3: rc = pick(osem_kernel<false, 32, true>); break;
+      case 4: rc = pick(osem_kernel<false, 16, true>); break;
+      case 5: rc = pick(osem_kernel<false, 8, true>); break;
+      case 6: rc = pick(osem_kernel<true, 32, false>); break;
+      case 7: rc = pick(osem_kernel<true, 16, false>); break;
+      case 8: rc = pick(osem_kernel<true, 8, false>); break;
+      case 9: rc = pick(osem_kernel<true, 32, true>); break;
+      case 10: rc = pick(osem_kernel<true, 16, true>); break;
+      default: rc = pick(osem_kernel<true, 8, true>); break;
+    }
     if (rc) return rc;
   }
+  if (!direct) {
+    // fold the back-projection quads into the back-projection image
+    if (tiled) {
+      rc = launch_quad_fold_tile(p, p.quads_bp, bp_img, 1, false, st);
+      if (rc) return rc;
+    } else if (res) {
+      osem_fold_kernel<<<aux_grid(nvox, 256), 256, 0, st>>>(p, wt);
+      count_launch();
+      JP_TRY_CUDA(cudaGetLastError());
+    } else {
+      osem_update_kernel<<<aux_grid(nvox, 256), 256, 0, st>>>(p, x);
+      count_launch();
+      JP_TRY_CUDA(cudaGetLastError());
+      return JP_OK;
+    }
+  }
   if (res) {
-    // z = fold(bp) into t; x <- x * (H^T z) / (s scale) on the last pass
-    // (passes t -> y -> t -> x; H^T = H for the symmetric taps)
-    osem_fold_kernel<<<aux_grid(nvox, 256), 256, 0, st>>>(p, wt);
-    count_launch();
-    JP_TRY_CUDA(cudaGetLastError());
+    // x <- x * (H^T bp) / (s scale) on the last pass (passes t -> y -> t ->
+    // x, bp in t; H^T = H for the symmetric taps)
     return gauss_passes(wt, wy, wt, x, 1, p.g, taps, sens, sens_scale, st);
   }
-  osem_update_kernel<<<aux_grid(nvox, 256), 256, 0, st>>>(p, x);
+  img_update_kernel<<<aux_grid(nvox, 256), 256, 0, st>>>(x, bp_img, sens, sens_scale, nvox);
   count_launch();
   JP_TRY_CUDA(cudaGetLastError());
   return JP_OK;
@@ -1242,7 +1528,7 @@ int osem_subset(jp_plan pl, int32_t f0, int32_t f1, float* x, const float* sens,
 
 extern "C" int jp_osem_subset_tof_lm(jp_plan pl, int32_t f0, int32_t f1, float* x, const float* sens,
                                      float sens_scale, float b, const jp_tof* t, void* stream) {
-  return osem_subset(pl, f0, f1, x, sens, sens_scale, b, nullptr, t, nullptr, nullptr, stream);
+  return osem_subset(pl, f0, f1, x, sens, sens_scale, b, nullptr, t, nullptr, JP_OSEM_PATH_AUTO, nullptr, stream);
 }
 
 extern "C" int jp_osem_subset_tof_lm_dev(jp_plan pl, int32_t f0, int32_t f1, float* x, const float* sens,
@@ -1251,17 +1537,13 @@ extern "C" int jp_osem_subset_tof_lm_dev(jp_plan pl, int32_t f0, int32_t f1, flo
     clear_error();
     return fail(JP_ERR_ARG, "b_dev is NULL");
   }
-  return osem_subset(pl, f0, f1, x, sens, sens_scale, 0.f, b_dev, t, nullptr, nullptr, stream);
+  return osem_subset(pl, f0, f1, x, sens, sens_scale, 0.f, b_dev, t, nullptr, JP_OSEM_PATH_AUTO, nullptr, stream);
 }
 
-extern "C" int jp_osem_subset_tof_lm_res(jp_plan pl, int32_t f0, int32_t f1, float* x, const float* sens,
-                                         float sens_scale, float b, const float* b_dev, const jp_tof* t,
-                                         const jp_resolution* r, float* work, void* stream) {
-  if (!r) {
-    jp::clear_error();
-    return jp::fail(JP_ERR_ARG, "resolution parameters are NULL");
-  }
-  return osem_subset(pl, f0, f1, x, sens, sens_scale, b, b_dev, t, r, work, stream);
+extern "C" int jp_osem_subset_tof_lm_ex(jp_plan pl, int32_t f0, int32_t f1, float* x, const float* sens,
+                                        float sens_scale, float b, const float* b_dev, const jp_tof* t,
+                                        const jp_resolution* r, int32_t path, float* work, void* stream) {
+  return osem_subset(pl, f0, f1, x, sens, sens_scale, b, b_dev, t, r, path, work, stream);
 }
 
 extern "C" int jp_fwd(jp_plan p, const float* img, int64_t s, float* proj, void* st) {

@@ -26,6 +26,8 @@ TOF_MODES = {"nontof": 0, "tof_sino": 1, "tof_lm": 2}
 JP_PLAN_KEEP_ORDER = 1
 JP_PLAN_TOF_EXACT = 2
 JP_PLAN_INTERLEAVED = 4
+OSEM_PATHS = {"auto": 0, "quads": 1, "direct": 2}
+OSEM_DIRECT_VOXELS_PER_EVENT = 32  # JP_OSEM_DIRECT_VOXELS_PER_EVENT
 
 
 class JosephError(RuntimeError):
@@ -77,7 +79,7 @@ _SIGS = {
     "jp_osem_subset_tof_lm": [P, I32, I32, P, P, F32, F32, P, P],
     "jp_osem_init": [P, P, I64, P],
     "jp_osem_subset_tof_lm_dev": [P, I32, I32, P, P, F32, P, P, P],
-    "jp_osem_subset_tof_lm_res": [P, I32, I32, P, P, F32, F32, P, P, P, P, P],
+    "jp_osem_subset_tof_lm_ex": [P, I32, I32, P, P, F32, F32, P, P, P, I32, P, P],
     "jp_gauss3d": [P, P, P, I32, P, P, P],
     "jp_poisson_loglik_value": [P, P, P, P, I64, P, P],
     "jp_poisson_loglik_grad": [P, P, P, P, P, I64, P, P],
@@ -432,21 +434,35 @@ def jp_osem_subset_tof_lm_dev(plan: Plan, f0: int, f1: int, x, sens, sens_scale:
     return x
 
 
-def jp_osem_subset_tof_lm_res(plan: Plan, f0: int, f1: int, x, sens, sens_scale: float, b, tof, fwhm_mm,
-                              work, truncate: float = 4.0, stream=None):
-    """Subset update with the resolution model H (Gaussian of ``fwhm_mm``):
-    x <- x / (sens*sens_scale) * H^T A_S^T (1/(A_S H x + b)), sens = H^T A^T 1.
-    ``b`` is a float, or a device float tensor (read when the kernels run,
-    capturable in a CUDA graph); ``work`` holds 2 images."""
+def jp_osem_subset_tof_lm_ex(plan: Plan, f0: int, f1: int, x, sens, sens_scale: float, b, tof, fwhm_mm=0.0,
+                             work=None, truncate: float = 4.0, path: str = "auto", stream=None):
+    """Subset update, general form: with the resolution model H (Gaussian of
+    ``fwhm_mm``; 0 = none) x <- x / (sens*sens_scale) * H^T A_S^T
+    (1/(A_S H x + b)), sens = H^T A^T 1.  ``b`` is a float, or a device
+    float tensor (read when the kernels run, capturable in a CUDA graph);
+    ``work`` holds 2 images (needed with the resolution model); ``path`` is
+    "auto", "quads" or "direct"."""
     t = tof_params(tof)
-    r = resolution(fwhm_mm, truncate)
+    r = None if (isinstance(fwhm_mm, (int, float)) and float(fwhm_mm) == 0.0) else resolution(fwhm_mm, truncate)
+    if r is not None and work is None:
+        raise ValueError("the resolution model needs a work tensor of 2 images")
+    if path not in OSEM_PATHS:
+        raise ValueError(f"path must be one of {sorted(OSEM_PATHS)}")
     b_dev = b if isinstance(b, torch.Tensor) else None
-    _check(load().jp_osem_subset_tof_lm_res(plan.handle, int(f0), int(f1), _ptr(x, torch.float32, "x"),
-                                            _ptr(sens, torch.float32, "sens"), float(sens_scale),
-                                            0.0 if b_dev is not None else float(b),
-                                            _ptr(b_dev, torch.float32, "b"), ctypes.byref(t), ctypes.byref(r),
-                                            _ptr(work, torch.float32, "work"), _stream(stream)))
+    _check(load().jp_osem_subset_tof_lm_ex(plan.handle, int(f0), int(f1), _ptr(x, torch.float32, "x"),
+                                           _ptr(sens, torch.float32, "sens"), float(sens_scale),
+                                           0.0 if b_dev is not None else float(b),
+                                           _ptr(b_dev, torch.float32, "b"), ctypes.byref(t),
+                                           None if r is None else ctypes.byref(r), OSEM_PATHS[path],
+                                           _ptr(work, torch.float32, "work"), _stream(stream)))
     return x
+
+
+def jp_osem_subset_tof_lm_res(plan: Plan, f0: int, f1: int, x, sens, sens_scale: float, b, tof, fwhm_mm,
+                              work, truncate: float = 4.0, path: str = "auto", stream=None):
+    """jp_osem_subset_tof_lm_ex with the resolution model of ``fwhm_mm``."""
+    return jp_osem_subset_tof_lm_ex(plan, f0, f1, x, sens, sens_scale, b, tof, fwhm_mm, work, truncate, path,
+                                    stream)
 
 
 def jp_gauss3d(img, geom, fwhm_mm, truncate: float = 4.0, out=None, work=None, stream=None):

@@ -4,8 +4,14 @@ x <- x / s_sub * A_S^T (1 / (A_S x + b)), subsets of the event stream).
 With the image-based resolution model of Sec. 3 (a 3D Gaussian of
 ``fwhm_mm``, 4.5 mm in the paper) the projector is A H and the update
 x <- x / s'_sub * H^T A_S^T (1 / (A_S H x + b)) uses s' = H^T A^T 1
-(``resolution_sensitivity``); one call of jp_osem_subset_tof_lm_res runs both
+(``resolution_sensitivity``); one call of jp_osem_subset_tof_lm_ex runs both
 convolutions, the fused projections and the update.
+
+Each subset update takes one of two paths (``path``): the plan's quad
+images (one 16-byte access per sample, an image-sized quad build / clear /
+fold per update) or the direct path (image gathers and scalar atomics, no
+quad traffic), which is cheaper for small subsets; "auto" picks by the
+subset's event count.
 
 The sensitivity image s = A^T 1 is the non-TOF back projection of every LOR
 of the scanner's span-1 sinogram; a frame's events are held in one plan
@@ -75,6 +81,7 @@ class FrameSpec:
     n_iter: int = 3
     n_sub: int = 8
     fwhm_mm: float = 0.0    # resolution model (0: none); sens must then be H^T A^T 1
+    path: str = "auto"      # subset update path: "auto", "quads" or "direct"
 
 
 class LMOSEMFrame:
@@ -112,12 +119,9 @@ class LMOSEMFrame:
     def _updates(self, n_iter):
         for _ in range(n_iter):
             for m in range(self.spec.n_sub):
-                if self.work is not None:
-                    ops.jp_osem_subset_tof_lm_res(self.plan, m, m + 1, self.x, self.sens, 1.0 / self.spec.n_sub,
-                                                  self.spec.b, self.tof, self.spec.fwhm_mm, self.work)
-                else:
-                    ops.jp_osem_subset_tof_lm(self.plan, m, m + 1, self.x, self.sens, 1.0 / self.spec.n_sub,
-                                              self.spec.b, self.tof)
+                ops.jp_osem_subset_tof_lm_ex(self.plan, m, m + 1, self.x, self.sens, 1.0 / self.spec.n_sub,
+                                             self.spec.b, self.tof, self.spec.fwhm_mm, self.work,
+                                             path=self.spec.path)
 
     def run(self):
         """All n_iter x n_sub subset updates, launched on the frame's stream."""

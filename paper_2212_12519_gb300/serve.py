@@ -183,7 +183,9 @@ class SlotGraph:
     """One OSEM iteration (n_sub subset updates) captured once per slot and
     image grid, replayed for every frame the slot serves.  The captured
     kernels read the subset ranges and b from device memory, so rebinding
-    the slot's plan to a new frame keeps the graph valid."""
+    the slot's plan to a new frame keeps the graph valid.  Two graphs are
+    captured, one per subset-update path (quad images / direct); a frame
+    replays the direct one when its subsets are small."""
 
     def __init__(self, plan: ops.Plan, sens: torch.Tensor, tof: synth.TofParams, geom: synth.ImageGeom,
                  n_sub: int, stream: torch.cuda.Stream, fwhm_mm: float = 0.0):
@@ -193,15 +195,15 @@ class SlotGraph:
         self.b = torch.zeros(1, dtype=torch.float32, device="cuda")
         self.work = (torch.empty((2,) + tuple(geom.shape), dtype=torch.float32, device="cuda")
                      if fwhm_mm > 0 else None)
-        self.graph = torch.cuda.CUDAGraph()
+        self.graphs = {}
         torch.cuda.synchronize()
-        with torch.cuda.graph(self.graph, stream=stream):
-            for m in range(n_sub):
-                if self.work is not None:
-                    ops.jp_osem_subset_tof_lm_res(plan, m, m + 1, self.x, sens, 1.0 / n_sub, self.b, tof, fwhm_mm,
-                                                  self.work)
-                else:
-                    ops.jp_osem_subset_tof_lm_dev(plan, m, m + 1, self.x, sens, 1.0 / n_sub, self.b, tof)
+        for path in ("quads", "direct"):
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                for m in range(n_sub):
+                    ops.jp_osem_subset_tof_lm_ex(plan, m, m + 1, self.x, sens, 1.0 / n_sub, self.b, tof, fwhm_mm,
+                                                 self.work, path=path)
+            self.graphs[path] = g
         torch.cuda.synchronize()
 
     def run(self, spec: osem.FrameSpec) -> torch.Tensor:
@@ -210,12 +212,17 @@ class SlotGraph:
             raise ValueError("subset count differs from the captured graph")
         if spec.fwhm_mm != self.fwhm_mm:
             raise ValueError("resolution model differs from the captured graph")
+        path = spec.path
+        if path == "auto":
+            nvox = int(np.prod(spec.geom.shape))
+            path = "direct" if n < (nvox // ops.OSEM_DIRECT_VOXELS_PER_EVENT) * spec.n_sub else "quads"
+        graph = self.graphs[path]
         with torch.cuda.stream(self.stream):
             ops.jp_plan_rebind(self.plan, spec.xs, spec.xe, [0] * spec.n_sub + [n], tof_bin=spec.tof_bin)
             self.b.fill_(float(spec.b))
             ops.jp_osem_init(self.x, self.sens)
             for _ in range(spec.n_iter):
-                self.graph.replay()
+                graph.replay()
             return self.x.clone()
 
 

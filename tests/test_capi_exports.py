@@ -79,7 +79,7 @@ def test_host_argument_checks(lib):
 
 
 def test_resolution_model_argument_checks(lib):
-    """jp_gauss3d / jp_osem_subset_tof_lm_res reject bad input on the host."""
+    """jp_gauss3d / jp_osem_subset_tof_lm_ex reject bad input on the host."""
     from paper_2212_12519_gb300 import ops
     ops.load()
     lib.jp_last_error.restype = ctypes.c_char_p
@@ -106,5 +106,17 @@ def test_resolution_model_argument_checks(lib):
     assert call(ok, out=4096 + nb + 2) == -2                        # misaligned
     assert call(ok, n=-1) == -1
     assert lib.jp_gauss3d(P(4096), P(4096 + nb), None, 1, ctypes.byref(g), ctypes.byref(ok), None) == -1
-    assert lib.jp_osem_subset_tof_lm_res(None, 0, 1, P(16), P(16), ctypes.c_float(1.0), ctypes.c_float(0.0),
-                                         None, None, None, P(16), None) == -1
+    assert lib.jp_osem_subset_tof_lm_ex(None, 0, 1, P(16), P(16), ctypes.c_float(1.0), ctypes.c_float(0.0),
+                                        None, None, None, 0, P(16), None) == -1
+
+
+def test_binding_constants_match_header():
+    """The Python mirrors of the header's #defines hold the same values."""
+    import re
+    from paper_2212_12519_gb300 import ops
+    with open(os.path.join(ROOT, "include", "joseph.h")) as f:
+        h = f.read()
+    defs = dict(re.findall(r"#define\s+(JP_\w+)\s+(\d+)", h))
+    assert int(defs["JP_OSEM_DIRECT_VOXELS_PER_EVENT"]) == ops.OSEM_DIRECT_VOXELS_PER_EVENT
+    assert {k: int(defs["JP_OSEM_PATH_" + k.upper()]) for k in ops.OSEM_PATHS} == ops.OSEM_PATHS
+    assert int(defs["JP_PLAN_INTERLEAVED"]) == ops.JP_PLAN_INTERLEAVED

@@ -40,15 +40,15 @@ def frame(geom, ph_spec, n, seed):
     return ph, xs, xe, tb, synth.background_level(ph, synth.TOF_CLINICAL)
 
 
-@pytest.mark.parametrize("graph", [False, True])
-def test_osem_frame_vs_oracle(ops, graph):
+@pytest.mark.parametrize("graph,path", [(False, "quads"), (True, "quads"), (False, "direct"), (True, "direct")])
+def test_osem_frame_vs_oracle(ops, graph, path):
     from paper_2212_12519_gb300 import osem
     g = synth.GEOM_OSEM_SMALL
     tof = synth.TOF_CLINICAL
     ph, xs, xe, tb, b = frame(g, synth.PHANTOM_OSEM_SMALL, 120_003, 5101)
     sens = smooth_sens(g, 5102)
     x_or = oracle.lm_osem(xs.numpy(), xe.numpy(), tb.numpy(), g, tof, sens, b, n_iter=3, n_sub=8, threads=8)
-    spec = osem.FrameSpec(xs.cuda(), xe.cuda(), tb.cuda(), g, b)
+    spec = osem.FrameSpec(xs.cuda(), xe.cuda(), tb.cuda(), g, b, path=path)
     fr = osem.LMOSEMFrame(spec, torch.from_numpy(sens).cuda(), tof)
     x = fr.run_graph() if graph else fr.run()
     torch.cuda.synchronize()

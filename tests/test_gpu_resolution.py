@@ -85,7 +85,7 @@ def res_frame():
     return g, ph, xs, xe, tb, s.astype(np.float32), synth.background_level(ph, synth.TOF_CLINICAL)
 
 
-@pytest.mark.parametrize("path", ["fused", "graph", "plain"])
+@pytest.mark.parametrize("path", ["fused", "graph", "plain", "direct", "direct_graph"])
 def test_osem_with_resolution_model_vs_oracle(ops, path):
     from paper_2212_12519_gb300 import osem
     g, ph, xs, xe, tb, s, b = res_frame()
@@ -97,13 +97,14 @@ def test_osem_with_resolution_model_vs_oracle(ops, path):
     # the library's own s' = H^T s agrees with the oracle's
     sens_gpu = osem.resolution_sensitivity(torch.from_numpy(s).cuda(), g, fwhm)
     assert max_err(sens_gpu.cpu().numpy(), s_eff) <= FWD_TOL
-    spec = osem.FrameSpec(xs.cuda(), xe.cuda(), tb.cuda(), g, b, n_iter=n_iter, n_sub=n_sub, fwhm_mm=fwhm)
+    spec = osem.FrameSpec(xs.cuda(), xe.cuda(), tb.cuda(), g, b, n_iter=n_iter, n_sub=n_sub, fwhm_mm=fwhm,
+                          path="direct" if path.startswith("direct") else "quads")
     sens = torch.from_numpy(s_eff).cuda()
     if path == "plain":
         x = osem.reconstruct_plain(spec, sens, tof)
     else:
         fr = osem.LMOSEMFrame(spec, sens, tof)
-        x = fr.run_graph() if path == "graph" else fr.run()
+        x = fr.run_graph() if path.endswith("graph") else fr.run()
     torch.cuda.synchronize()
     assert rel_l2(x.cpu().numpy(), x_or) <= OSEM_TOL
     # voxels without sensitivity stay 0
@@ -112,8 +113,9 @@ def test_osem_with_resolution_model_vs_oracle(ops, path):
 
 
 def test_slot_graph_with_resolution_model(ops):
-    """A per-slot graph captured once with the resolution model serves two
-    different frames after rebinding; each equals its own direct run."""
+    """Per-slot graphs captured once with the resolution model serve two
+    different frames after rebinding; each equals its own direct run, on
+    both subset-update paths."""
     from paper_2212_12519_gb300 import osem, serve
     g, ph, xs, xe, tb, s, b = res_frame()
     tof = synth.TOF_CLINICAL
@@ -125,6 +127,9 @@ def test_slot_graph_with_resolution_model(ops):
                               fwhm_mm=4.5)
         x_graph = srv.slot_graphs[(0, g.shape)].run(spec)
         x_direct = osem.LMOSEMFrame(spec, sens, tof).run()
+        spec.path = "quads"
+        x_graph_q = srv.slot_graphs[(0, g.shape)].run(spec)
         torch.cuda.synchronize()
         assert rel_l2(x_graph.cpu().numpy(), x_direct.cpu().numpy()) <= 1e-5
+        assert rel_l2(x_graph_q.cpu().numpy(), x_direct.cpu().numpy()) <= 1e-5
     srv.close()
