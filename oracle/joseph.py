@@ -52,6 +52,13 @@ def load(mutant: int = 0):
         lib.or_fwd.restype = ctypes.c_int
         lib.or_back.argtypes = [P, P, I64, P, P, P, ctypes.c_int, P, I64, P, P, P, P, ctypes.c_int]
         lib.or_back.restype = ctypes.c_int
+        D = ctypes.c_double
+        lib.or_fwd_ex.argtypes = [P, P, I64, P, P, P, ctypes.c_int, P, I64, P, P, P, P, I64, D, P, P, P,
+                                  ctypes.c_int]
+        lib.or_fwd_ex.restype = ctypes.c_int
+        lib.or_back_ex.argtypes = [P, P, I64, P, P, P, ctypes.c_int, P, I64, P, P, P, P, I64, D, P, P,
+                                   ctypes.c_int]
+        lib.or_back_ex.restype = ctypes.c_int
         lib.or_tof_weight.argtypes = [ctypes.c_double] * 5
         lib.or_tof_weight.restype = ctypes.c_double
         lib.or_principal_axis.argtypes = [P, P]
@@ -84,6 +91,15 @@ def _tof(tof, amb_eps):
     return _d([tof.bin_width, tof.sigma, tof.n_sigmas, amb_eps]), int(tof.n_bins)
 
 
+def _table(tof):
+    """(table, nodes, half width) of a tabulated TOF kernel, or (None, 0, 0)."""
+    kernel = getattr(tof, "kernel", None) if tof is not None else None
+    if kernel is None:
+        return None, 0, 0.0
+    t = _d(kernel)
+    return t, int(t.size), float(tof.kernel_half_width)
+
+
 def _common(xs, xe, mode, tof_bin, delta):
     xs = _d(xs).reshape(-1, 3)
     xe = _d(xe).reshape(-1, 3)
@@ -97,11 +113,14 @@ def _common(xs, xe, mode, tof_bin, delta):
 
 
 def fwd(xs, xe, img, geom, mode="nontof", tof=None, tof_bin=None, delta=None,
-        threads=1, amb_eps=0.0, return_amb=False, mutant=0):
+        threads=1, amb_eps=0.0, return_amb=False, mutant=0, sigma=None):
     """Forward projection (FP64).  Returns [n] or [n, n_bins] (TOF sinogram);
-    with ``return_amb`` also the per-output ambiguity magnitude."""
+    with ``return_amb`` also the per-output ambiguity magnitude.  ``sigma``:
+    optional per-LOR Gaussian sigma; a tabulated kernel comes with ``tof``."""
     lib = load(mutant)
     xs, xe, n, m, tb, de = _common(xs, xe, mode, tof_bin, delta)
+    sg = None if sigma is None else _d(sigma).reshape(n)
+    tab, tn, thw = _table(tof)
     ng, og, vg = _geom(geom)
     img = _d(img).reshape(-1)
     if img.size != int(np.prod(ng)):
@@ -110,8 +129,9 @@ def fwd(xs, xe, img, geom, mode="nontof", tof=None, tof_bin=None, delta=None,
     nout = nb if m == 1 else 1
     out = np.zeros(n * nout, dtype=np.float64)
     amb = np.zeros(n * nout, dtype=np.float64) if return_amb else None
-    rc = lib.or_fwd(_ptr(xs), _ptr(xe), n, _ptr(ng), _ptr(og), _ptr(vg), m, _ptr(tp), nb,
-                    _ptr(tb), _ptr(de), _ptr(img), _ptr(out), _ptr(amb), int(threads))
+    rc = lib.or_fwd_ex(_ptr(xs), _ptr(xe), n, _ptr(ng), _ptr(og), _ptr(vg), m, _ptr(tp), nb,
+                       _ptr(tb), _ptr(de), _ptr(sg), _ptr(tab), tn, thw, _ptr(img), _ptr(out), _ptr(amb),
+                       int(threads))
     if rc != 0:
         raise ValueError(f"or_fwd failed ({rc})")
     shape = (n, nout) if m == 1 else (n,)
@@ -121,10 +141,12 @@ def fwd(xs, xe, img, geom, mode="nontof", tof=None, tof_bin=None, delta=None,
 
 
 def back(xs, xe, y, geom, mode="nontof", tof=None, tof_bin=None, delta=None, threads=1,
-         mutant=0):
+         mutant=0, sigma=None):
     """Back projection A^T y (FP64), returned as an image of ``geom.shape``."""
     lib = load(mutant)
     xs, xe, n, m, tb, de = _common(xs, xe, mode, tof_bin, delta)
+    sg = None if sigma is None else _d(sigma).reshape(n)
+    tab, tn, thw = _table(tof)
     ng, og, vg = _geom(geom)
     tp, nb = _tof(tof, 0.0)
     nin = nb if m == 1 else 1
@@ -132,8 +154,8 @@ def back(xs, xe, y, geom, mode="nontof", tof=None, tof_bin=None, delta=None, thr
     if y.size != n * nin:
         raise ValueError("y size mismatch")
     img = np.zeros(int(np.prod(ng)), dtype=np.float64)
-    rc = lib.or_back(_ptr(xs), _ptr(xe), n, _ptr(ng), _ptr(og), _ptr(vg), m, _ptr(tp), nb,
-                     _ptr(tb), _ptr(de), _ptr(y), _ptr(img), int(threads))
+    rc = lib.or_back_ex(_ptr(xs), _ptr(xe), n, _ptr(ng), _ptr(og), _ptr(vg), m, _ptr(tp), nb,
+                        _ptr(tb), _ptr(de), _ptr(sg), _ptr(tab), tn, thw, _ptr(y), _ptr(img), int(threads))
     if rc != 0:
         raise ValueError(f"or_back failed ({rc})")
     return img.reshape(tuple(int(s) for s in ng))

@@ -21,7 +21,13 @@
  *      when |tau - c| <= n_sigmas s + D/2, else 0 (Gaussian of width s
  *      convolved with a bin of width D, truncated).  Sinogram bin t of N has
  *      c_t = (t - (N-1)/2) D + delta; a listmode event with signed bin t_s has
- *      c = t_s D + delta (delta: optional per-LOR TOF centre offset);
+ *      c = t_s D + delta (delta: optional per-LOR TOF centre offset).  An
+ *      optional per-LOR sigma replaces s for that LOR (per-event TOF
+ *      resolution);
+ *   5b. tabulated kernel (Sec. 5: a 1D lookup table permits non-Gaussian
+ *      TOF kernels): with a table of n values at d_e = -h + e 2h/(n-1), the
+ *      weight at d = tau - c is the linear interpolation of the table, and 0
+ *      when |d| > h (replacing the Gaussian and its truncation);
  *   6. back projection is the exact transpose (Sec. 2.2, matched pair).
  *
  * All arithmetic is double.  Outputs are double.  The single-thread mode is
@@ -60,6 +66,9 @@ typedef struct {
   double n_sigmas;
   int64_t n_bins;     /* N (sinogram) */
   double amb_eps;     /* ambiguity band half-width (mm) */
+  const double* table;  /* tabulated kernel or NULL (Gaussian) */
+  int64_t table_nodes;
+  double table_hw;      /* h */
 } tof_t;
 
 /* ---------------------------------------------------------------------- */
@@ -115,13 +124,41 @@ double or_tof_weight(double tau, double centre, double bin_width, double sigma,
 #endif
 }
 
+/* tabulated kernel: linear interpolation of the nodes, clamped to the table
+ * (callers apply the support rule |dist| <= h) */
+static double table_value(const tof_t* t, double dist) {
+#if OR_MUTANT == 8
+  /* planted: node spacing 2h / n instead of 2h / (n - 1) */
+  double x = (dist + t->table_hw) * (double)(t->table_nodes) / (2.0 * t->table_hw);
+#else
+  double x = (dist + t->table_hw) * (double)(t->table_nodes - 1) / (2.0 * t->table_hw);
+#endif
+  double fl = floor(x);
+  int64_t i = (int64_t)fl;
+  if (i < 0) i = 0;
+  if (i > t->table_nodes - 2) i = t->table_nodes - 2;
+  double fr = x - (double)i;
+  return t->table[i] + fr * (t->table[i + 1] - t->table[i]);
+}
+
+/* TOF weight of a bin with centre `centre` for a sample at tau, with the LOR's
+ * sigma (Gaussian) or the table */
+static double tof_w(const tof_t* t, double tau, double centre, double sigma) {
+  if (t->table) {
+    double dist = tau - centre;
+    return fabs(dist) > t->table_hw ? 0.0 : table_value(t, dist);
+  }
+  return or_tof_weight(tau, centre, t->bin_width, sigma, t->n_sigmas);
+}
+
 /* untruncated value and ambiguity flag */
-static double tof_weight_amb(double tau, double centre, const tof_t* t, int* amb) {
+static double tof_weight_amb(double tau, double centre, const tof_t* t, double sigma, int* amb) {
   double dist = tau - centre;
-  double r = t->n_sigmas * t->sigma + 0.5 * t->bin_width;
+  double r = t->table ? t->table_hw : t->n_sigmas * sigma + 0.5 * t->bin_width;
   *amb = fabs(fabs(dist) - r) <= t->amb_eps;
   if (fabs(dist) > r && !*amb) return 0.0;
-  double k = 1.0 / (sqrt(2.0) * t->sigma);
+  if (t->table) return table_value(t, dist);
+  double k = 1.0 / (sqrt(2.0) * sigma);
   double g = 0.5 * (erf((dist + 0.5 * t->bin_width) * k) - erf((dist - 0.5 * t->bin_width) * k));
   return g; /* caller applies the truncation rule itself for the main value */
 }
@@ -237,7 +274,7 @@ static void scatter(const sample_t* s, double val, double* img) {
 /* per-LOR forward / back                                                   */
 /* ---------------------------------------------------------------------- */
 static void fwd_one(const double* xs, const double* xe, const geom_t* g, const tof_t* t,
-                    int64_t tof_bin, double delta, const double* img, double* out,
+                    int64_t tof_bin, double delta, double sigma, const double* img, double* out,
                     double* amb) {
   int nout = (t->mode == 1) ? (int)t->n_bins : 1;
   for (int q = 0; q < nout; ++q) {
@@ -256,15 +293,15 @@ static void fwd_one(const double* xs, const double* xe, const geom_t* g, const t
       for (int64_t b = 0; b < t->n_bins; ++b) {
         double cb = bin_centre_sino(b, t, delta);
         int ambf = 0;
-        double graw = tof_weight_amb(s.tau, cb, t, &ambf);
-        out[b] += or_tof_weight(s.tau, cb, t->bin_width, t->sigma, t->n_sigmas) * sk;
+        double graw = tof_weight_amb(s.tau, cb, t, sigma, &ambf);
+        out[b] += tof_w(t, s.tau, cb, sigma) * sk;
         if (amb && ambf) amb[b] += fabs(graw * sk);
       }
     } else {
       double cb = (double)tof_bin * t->bin_width + delta;
       int ambf = 0;
-      double graw = tof_weight_amb(s.tau, cb, t, &ambf);
-      out[0] += or_tof_weight(s.tau, cb, t->bin_width, t->sigma, t->n_sigmas) * sk;
+      double graw = tof_weight_amb(s.tau, cb, t, sigma, &ambf);
+      out[0] += tof_w(t, s.tau, cb, sigma) * sk;
       if (amb && ambf) amb[0] += fabs(graw * sk);
     }
   }
@@ -275,7 +312,7 @@ static void fwd_one(const double* xs, const double* xe, const geom_t* g, const t
 }
 
 static void back_one(const double* xs, const double* xe, const geom_t* g, const tof_t* t,
-                     int64_t tof_bin, double delta, const double* y, double* img) {
+                     int64_t tof_bin, double delta, double sigma, const double* y, double* img) {
   ray_t r = ray_setup(xs, xe, g);
   if (!r.valid) return;
   sample_t s;
@@ -287,11 +324,9 @@ static void back_one(const double* xs, const double* xe, const geom_t* g, const 
     } else if (t->mode == 1) {
       val = 0.0;
       for (int64_t b = 0; b < t->n_bins; ++b)
-        val += or_tof_weight(s.tau, bin_centre_sino(b, t, delta), t->bin_width, t->sigma,
-                             t->n_sigmas) * y[b];
+        val += tof_w(t, s.tau, bin_centre_sino(b, t, delta), sigma) * y[b];
     } else {
-      val = or_tof_weight(s.tau, (double)tof_bin * t->bin_width + delta, t->bin_width,
-                          t->sigma, t->n_sigmas) * y[0];
+      val = tof_w(t, s.tau, (double)tof_bin * t->bin_width + delta, sigma) * y[0];
     }
     scatter(&s, r.w0 * val, img);
   }
@@ -301,7 +336,7 @@ static void back_one(const double* xs, const double* xe, const geom_t* g, const 
 /* threaded drivers                                                         */
 /* ---------------------------------------------------------------------- */
 typedef struct {
-  const double *xs, *xe, *img, *y, *delta;
+  const double *xs, *xe, *img, *y, *delta, *sigma;
   const int64_t* tof_bin;
   double *out, *amb, *img_out;
   const geom_t* g;
@@ -313,9 +348,16 @@ static void* fwd_job(void* p) {
   job_t* j = (job_t*)p;
   int nout = (j->t->mode == 1) ? (int)j->t->n_bins : 1;
   for (int64_t i = j->lo; i < j->hi; ++i)
+#if OR_MUTANT == 9
+    /* planted: the per-LOR sigma is ignored */
     fwd_one(j->xs + 3 * i, j->xe + 3 * i, j->g, j->t, j->tof_bin ? j->tof_bin[i] : 0,
-            j->delta ? j->delta[i] : 0.0, j->img, j->out + nout * i,
+            j->delta ? j->delta[i] : 0.0, j->t->sigma, j->img, j->out + nout * i,
             j->amb ? j->amb + nout * i : NULL);
+#else
+    fwd_one(j->xs + 3 * i, j->xe + 3 * i, j->g, j->t, j->tof_bin ? j->tof_bin[i] : 0,
+            j->delta ? j->delta[i] : 0.0, j->sigma ? j->sigma[i] : j->t->sigma, j->img, j->out + nout * i,
+            j->amb ? j->amb + nout * i : NULL);
+#endif
   return NULL;
 }
 
@@ -324,12 +366,14 @@ static void* back_job(void* p) {
   int nin = (j->t->mode == 1) ? (int)j->t->n_bins : 1;
   for (int64_t i = j->lo; i < j->hi; ++i)
     back_one(j->xs + 3 * i, j->xe + 3 * i, j->g, j->t, j->tof_bin ? j->tof_bin[i] : 0,
-             j->delta ? j->delta[i] : 0.0, j->y + nin * i, j->img_out);
+             j->delta ? j->delta[i] : 0.0, j->sigma ? j->sigma[i] : j->t->sigma, j->y + nin * i,
+             j->img_out);
   return NULL;
 }
 
 static int fill(geom_t* g, tof_t* t, const int64_t* n, const double* o, const double* v,
-                int mode, const double* tofp, int64_t n_bins) {
+                int mode, const double* tofp, int64_t n_bins, const double* table,
+                int64_t table_nodes, double table_hw) {
   for (int i = 0; i < 3; ++i) {
     if (n[i] <= 0 || !(v[i] > 0)) return -1;
     g->n[i] = n[i];
@@ -342,8 +386,13 @@ static int fill(geom_t* g, tof_t* t, const int64_t* n, const double* o, const do
   t->n_sigmas = tofp ? tofp[2] : 3.0;
   t->amb_eps = tofp ? tofp[3] : 0.0;
   t->n_bins = n_bins;
+  t->table = table;
+  t->table_nodes = table_nodes;
+  t->table_hw = table_hw;
   if (mode < 0 || mode > 2) return -1;
-  if (mode != 0 && (!(t->bin_width > 0) || !(t->sigma > 0) || !(t->n_sigmas > 0))) return -1;
+  if (mode != 0 && !(t->bin_width > 0)) return -1;
+  if (mode != 0 && table && (table_nodes < 2 || !(table_hw > 0))) return -1;
+  if (mode != 0 && !table && (!(t->sigma > 0) || !(t->n_sigmas > 0))) return -1;
   if (mode == 1 && n_bins <= 0) return -1;
   return 0;
 }
@@ -357,17 +406,20 @@ static int fill(geom_t* g, tof_t* t, const int64_t* n, const double* o, const do
  *   n_bins   sinogram TOF bins (mode 1)
  *   tof_bin  [nlor] signed listmode bins (mode 2) or NULL
  *   delta    [nlor] TOF centre offsets or NULL (0)
+ *   sigma    [nlor] per-LOR Gaussian sigma or NULL (tofp[1] for every LOR)
+ *   table, table_nodes, table_hw   tabulated TOF kernel (5b) or NULL
  *   img      [n0*n1*n2] double image
  *   out      [nlor] or [nlor*n_bins] (TOF fastest)
  *   amb      same shape as out, or NULL
  */
-int or_fwd(const double* xs, const double* xe, int64_t nlor, const int64_t* n,
-           const double* o, const double* v, int mode, const double* tofp, int64_t n_bins,
-           const int64_t* tof_bin, const double* delta, const double* img, double* out,
-           double* amb, int nthreads) {
+int or_fwd_ex(const double* xs, const double* xe, int64_t nlor, const int64_t* n,
+              const double* o, const double* v, int mode, const double* tofp, int64_t n_bins,
+              const int64_t* tof_bin, const double* delta, const double* sigma,
+              const double* table, int64_t table_nodes, double table_hw, const double* img,
+              double* out, double* amb, int nthreads) {
   geom_t g;
   tof_t t;
-  if (fill(&g, &t, n, o, v, mode, tofp, n_bins)) return -1;
+  if (fill(&g, &t, n, o, v, mode, tofp, n_bins, table, table_nodes, table_hw)) return -1;
   if (mode == 2 && !tof_bin) return -1;
   if (nthreads < 1) nthreads = 1;
   if (nthreads > 256) nthreads = 256;
@@ -375,7 +427,7 @@ int or_fwd(const double* xs, const double* xe, int64_t nlor, const int64_t* n,
   job_t jobs[256];
   pthread_t th[256];
   for (int i = 0; i < nthreads; ++i) {
-    job_t j = {xs, xe, img, NULL, delta, tof_bin, out, amb, NULL, &g, &t,
+    job_t j = {xs, xe, img, NULL, delta, sigma, tof_bin, out, amb, NULL, &g, &t,
                nlor * i / nthreads, nlor * (i + 1) / nthreads};
     jobs[i] = j;
   }
@@ -392,13 +444,14 @@ int or_fwd(const double* xs, const double* xe, int64_t nlor, const int64_t* n,
  * or_back: img_out += A^T y  (accumulates; double image of n0*n1*n2).
  * y is [nlor] (modes 0, 2) or [nlor*n_bins] (mode 1).
  */
-int or_back(const double* xs, const double* xe, int64_t nlor, const int64_t* n,
-            const double* o, const double* v, int mode, const double* tofp, int64_t n_bins,
-            const int64_t* tof_bin, const double* delta, const double* y, double* img_out,
-            int nthreads) {
+int or_back_ex(const double* xs, const double* xe, int64_t nlor, const int64_t* n,
+               const double* o, const double* v, int mode, const double* tofp, int64_t n_bins,
+               const int64_t* tof_bin, const double* delta, const double* sigma,
+               const double* table, int64_t table_nodes, double table_hw, const double* y,
+               double* img_out, int nthreads) {
   geom_t g;
   tof_t t;
-  if (fill(&g, &t, n, o, v, mode, tofp, n_bins)) return -1;
+  if (fill(&g, &t, n, o, v, mode, tofp, n_bins, table, table_nodes, table_hw)) return -1;
   if (mode == 2 && !tof_bin) return -1;
   if (nthreads < 1) nthreads = 1;
   if (nthreads > 256) nthreads = 256;
@@ -412,7 +465,7 @@ int or_back(const double* xs, const double* xe, int64_t nlor, const int64_t* n,
     if (!priv) return -2;
   }
   for (int i = 0; i < nthreads; ++i) {
-    job_t j = {xs, xe, NULL, y, delta, tof_bin, NULL, NULL,
+    job_t j = {xs, xe, NULL, y, delta, sigma, tof_bin, NULL, NULL,
                nthreads > 1 ? priv + (size_t)nvox * i : img_out, &g, &t,
                nlor * i / nthreads, nlor * (i + 1) / nthreads};
     jobs[i] = j;
@@ -435,3 +488,20 @@ int or_back(const double* xs, const double* xe, int64_t nlor, const int64_t* n,
 int or_principal_axis(const double* xs, const double* xe) { return principal_axis(xs, xe); }
 
 int or_mutant(void) { return OR_MUTANT; }
+
+/* the Gaussian-kernel forms with one sigma for every LOR */
+int or_fwd(const double* xs, const double* xe, int64_t nlor, const int64_t* n,
+           const double* o, const double* v, int mode, const double* tofp, int64_t n_bins,
+           const int64_t* tof_bin, const double* delta, const double* img, double* out,
+           double* amb, int nthreads) {
+  return or_fwd_ex(xs, xe, nlor, n, o, v, mode, tofp, n_bins, tof_bin, delta, NULL, NULL, 0, 0.0,
+                   img, out, amb, nthreads);
+}
+
+int or_back(const double* xs, const double* xe, int64_t nlor, const int64_t* n,
+            const double* o, const double* v, int mode, const double* tofp, int64_t n_bins,
+            const int64_t* tof_bin, const double* delta, const double* y, double* img_out,
+            int nthreads) {
+  return or_back_ex(xs, xe, nlor, n, o, v, mode, tofp, n_bins, tof_bin, delta, NULL, NULL, 0, 0.0,
+                    y, img_out, nthreads);
+}

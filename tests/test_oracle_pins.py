@@ -683,3 +683,107 @@ def test_sino_osem_fixed_point_and_counts(mode):
     # zero expected counts (A x + c = 0 on a LOR) contribute 0, not NaN
     x2 = oracle.sino_osem_subset_update(np.zeros(g.shape), xs, xe, y, np.zeros_like(c), sens, g, mode, tof)
     assert np.all(np.isfinite(x2)) and np.all(x2 == 0.0)
+
+
+# ---------------------------------------------------------------------------
+# tabulated (non-Gaussian) TOF kernels and per-LOR sigma (paper Sec. 5)
+# ---------------------------------------------------------------------------
+def _tof_ext_pins(mutant=0):
+    """Pins of the tabulated-kernel and per-LOR-sigma paths; returns the
+    names of the pins that failed."""
+    failed = []
+    g = G((12, 10, 9), (-5.5, -4.1, -3.7), (1.0, 0.9, 1.1))
+    xs, xe = synth.random_lors(60, g, seed=151)
+    rng = np.random.Generator(np.random.PCG64(152))
+    x = rng.uniform(0.2, 1.5, size=g.shape)
+    p_non = oracle.fwd(xs, xe, x, g, "nontof", mutant=mutant)
+    # (1) the triangle of half-width D (nodes 0, 1, 0) is a partition of
+    #     unity over bins spaced D: summed over enough sinogram bins the TOF
+    #     projection is the non-TOF one
+    D = 1.7
+    tri = synth.TofParams.tabulated(D, 41, (0.0, 1.0, 0.0), D)
+    p_tri = oracle.fwd(xs, xe, x, g, "tof_sino", tri, mutant=mutant)
+    if np.abs(p_tri.sum(axis=1) - p_non).max() > 1e-12 * p_non.max():
+        failed.append("triangle-partition")
+    # (2) a 5-node table of the triangle (nodes 0, .5, 1, .5, 0) is the same
+    #     function: the node positions are -h + e 2h / (n - 1)
+    tri5 = synth.TofParams.tabulated(D, 41, (0.0, 0.5, 1.0, 0.5, 0.0), D)
+    if np.abs(oracle.fwd(xs, xe, x, g, "tof_sino", tri5, mutant=mutant) - p_tri).max() > 1e-13 * p_non.max():
+        failed.append("table-nodes")
+    # (3) a box of width D (value 1 inside +-D/2): an axis-aligned ray along
+    #     axis 0 through a uniform image collects v_0 per voxel centre inside
+    #     the window
+    box = synth.TofParams.tabulated(D, 1, (1.0, 1.0), D / 2)
+    ones = np.ones(g.shape)
+    y0 = g.origin[1] + 4 * g.voxsize[1]
+    z0 = g.origin[2] + 3 * g.voxsize[2]
+    a = (-20.0, y0, z0)
+    b = (20.0, y0, z0)
+    cen = 0.7
+    p_box = oracle.fwd([a], [b], ones, g, "tof_lm", box, tof_bin=[0], delta=[cen], mutant=mutant)[0]
+    xc = g.origin[0] + np.arange(g.shape[0]) * g.voxsize[0]  # tau of the voxel centres (midpoint at 0)
+    expect = g.voxsize[0] * np.sum(np.abs(xc - cen) <= D / 2)
+    if abs(p_box - expect) > 1e-12:
+        failed.append("box-window")
+    # (4) an asymmetric table: swapping the endpoints and negating the bin
+    #     mirrors the distance, so the reversed table gives the same value
+    asym = synth.TofParams.tabulated(D, 1, (0.0, 0.2, 1.0, 0.6, 0.1), 2.5)
+    mirr = synth.TofParams.tabulated(D, 1, (0.1, 0.6, 1.0, 0.2, 0.0), 2.5)
+    tb = rng.integers(-3, 4, size=len(xs))
+    p_a = oracle.fwd(xs, xe, x, g, "tof_lm", asym, tof_bin=tb, mutant=mutant)
+    p_m = oracle.fwd(xe, xs, x, g, "tof_lm", mirr, tof_bin=-tb, mutant=mutant)
+    if np.abs(p_a - p_m).max() > 1e-12 * max(p_a.max(), 1e-30):
+        failed.append("table-mirror")
+    # (5) per-LOR sigma: each LOR equals the single-sigma projection with its
+    #     own sigma
+    tof = T(bin_width=1.3, sigma=1.1, n_sigmas=3.0, n_bins=7)
+    sig = rng.uniform(0.6, 2.4, size=len(xs))
+    p_s = oracle.fwd(xs, xe, x, g, "tof_lm", tof, tof_bin=tb, sigma=sig, mutant=mutant)
+    for i in (0, 7, 31, 59):
+        ti = T(bin_width=1.3, sigma=float(sig[i]), n_sigmas=3.0, n_bins=7)
+        pi = oracle.fwd(xs[i:i + 1], xe[i:i + 1], x, g, "tof_lm", ti, tof_bin=tb[i:i + 1], mutant=mutant)[0]
+        if abs(p_s[i] - pi) > 1e-13 * max(abs(pi), 1e-30):
+            failed.append("per-lor-sigma")
+            break
+    return failed
+
+
+def test_tabulated_kernel_and_per_lor_sigma_pins():
+    assert _tof_ext_pins() == []
+
+
+@pytest.mark.parametrize("mode", ["tof_sino", "tof_lm"])
+def test_tabulated_kernel_adjoint_and_gaussian_table(mode):
+    """The tabulated path is a matched pair, and a fine table of the
+    Gaussian bin response reproduces the Gaussian kernel within the linear
+    interpolation bound h^2/8 max|g''|; g'' is a difference of two Gaussian
+    pdf derivatives, so |g''| <= 2 / (sigma^2 sqrt(2 pi e))."""
+    g = G((9, 11, 8), (-4.0, -5.0, -3.5), (1.0, 1.0, 1.0))
+    gt = T(bin_width=1.5, sigma=1.2, n_sigmas=3.0, n_bins=9)
+    R = gt.n_sigmas * gt.sigma + gt.bin_width / 2
+    nodes = 2001
+    d = np.linspace(-R, R, nodes)
+    vals = [oracle.tof_weight(float(v), 0.0, gt.bin_width, gt.sigma, 50.0) for v in d]
+    tab = synth.TofParams.tabulated(gt.bin_width, gt.n_bins, vals, R)
+    xs, xe = synth.random_lors(80, g, seed=161)
+    rng = np.random.Generator(np.random.PCG64(162))
+    tb = rng.integers(-3, 4, size=len(xs)) if mode == "tof_lm" else None
+    x = rng.uniform(0.0, 1.0, size=g.shape)
+    pt = oracle.fwd(xs, xe, x, g, mode, tab, tof_bin=tb)
+    pg = oracle.fwd(xs, xe, x, g, mode, gt, tof_bin=tb)
+    h = 2 * R / (nodes - 1)
+    bound = h * h / 8 * 2 / (gt.sigma ** 2 * math.sqrt(2 * math.pi * math.e))
+    # per sample the weights differ by <= bound (inside the support; at the
+    # edge both truncate at R), so a projection by <= bound * sum of |samples|
+    p_abs = oracle.fwd(xs, xe, x, g, "nontof")
+    assert np.all(np.abs(pt - pg).reshape(len(xs), -1).max(axis=1) <= bound * p_abs + 1e-12)
+    y = rng.uniform(0.0, 1.0, size=pt.shape)
+    lhs = float(np.sum(pt * y))
+    rhs = float(np.sum(x * oracle.back(xs, xe, y, g, mode, tab, tof_bin=tb)))
+    assert lhs == pytest.approx(rhs, rel=1e-12)
+
+
+def test_tabulated_and_sigma_planted_mistakes():
+    for mutant in (8, 9):
+        oracle.joseph.build(mutant)
+        assert _tof_ext_pins(mutant), f"planted mistake {mutant} not caught"
