@@ -73,12 +73,24 @@ typedef struct {
 } jp_image_geom;
 
 /* TOF kernel: bin width (mm), Gaussian sigma (mm, = FWHM / 2.35482),
- * truncation in sigmas, number of sinogram TOF bins (unused in listmode). */
+ * truncation in sigmas, number of sinogram TOF bins (unused in listmode).
+ *
+ * Optional tabulated kernel (paper Sec. 5: a 1D lookup table allows
+ * non-Gaussian TOF kernels): when `kernel` is non-NULL it is a device array
+ * of `kernel_nodes` float32 values (2 .. JP_TOF_TABLE) of the bin response
+ * at the signed distances d_e = -h + e * 2h / (kernel_nodes - 1) from the bin
+ * centre (h = kernel_half_width > 0).  A sample at distance d then weighs
+ * the linear interpolation of the table, and 0 where |d| > h; sigma and
+ * n_sigmas are ignored.  The table must stay valid while calls that use it
+ * run. */
 typedef struct {
   float bin_width;
   float sigma;
   float n_sigmas;
   int32_t n_bins;
+  const float* kernel;
+  int32_t kernel_nodes;
+  float kernel_half_width;
 } jp_tof;
 
 /* Plan options (zero-initialise for defaults).  A plan sorts its LORs into
@@ -158,6 +170,21 @@ int jp_plan_create(jp_plan* out, const float* xstart, const float* xend,
 int jp_plan_rebind(jp_plan p, const float* xstart, const float* xend, const int16_t* tof_bin,
                    const float* tof_center_offset, const int64_t* frame_offsets,
                    int32_t n_frames, void* stream);
+
+/*
+ * jp_plan_set_event_sigma -- per-event TOF resolution for a TOF-listmode
+ * plan: sigma is a device float32 array of the bound LORs' Gaussian sigmas
+ * (mm) in caller order (n_total entries); it is gathered into the plan's
+ * binned order (storage allocated on the first call, `capacity` floats).
+ * Listmode projections and OSEM updates of the plan then use, per event,
+ * k = 1/(sqrt2 sigma_e) and the window n_sigmas sigma_e + bin_width / 2
+ * (values <= 0 keep the jp_tof sigma), on the exact erf path (the TOF table
+ * holds a single sigma); a tabulated kernel ignores sigma.  Rebinding the
+ * plan clears it; sigma = NULL clears it.  TOF-sinogram projections of a
+ * plan with per-event sigma fail with JP_ERR_STATE.
+ * Errors: JP_ERR_ARG, JP_ERR_ALIGN, JP_ERR_NOMEM, JP_ERR_CUDA.
+ */
+int jp_plan_set_event_sigma(jp_plan p, const float* sigma, void* stream);
 
 /* releases the plan's device memory (synchronises the device first) */
 int jp_plan_destroy(jp_plan p);

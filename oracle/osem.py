@@ -28,15 +28,16 @@ def _subset(arrs, m, n_sub):
 
 
 def lm_osem_subset_update(x, xs, xe, tof_bin, geom, tof, sens, b, m, n_sub, threads=1, fwhm_mm=0.0,
-                          truncate=4.0):
+                          truncate=4.0, sigma=None):
     """One subset update of TOF listmode OSEM (double precision), with the
-    resolution model when ``fwhm_mm`` > 0."""
-    sxs, sxe, stb = _subset([xs, xe, tof_bin], m, n_sub)
+    resolution model when ``fwhm_mm`` > 0 and per-event TOF sigma when
+    ``sigma`` is given."""
+    sxs, sxe, stb, ssg = _subset([xs, xe, tof_bin, sigma], m, n_sub)
     res = np.any(np.asarray(fwhm_mm, dtype=np.float64) > 0)
     y = resolution.gauss3d(x, geom, fwhm_mm, truncate) if res else x
-    p = joseph.fwd(sxs, sxe, y, geom, mode="tof_lm", tof=tof, tof_bin=stb, threads=threads)
+    p = joseph.fwd(sxs, sxe, y, geom, mode="tof_lm", tof=tof, tof_bin=stb, threads=threads, sigma=ssg)
     q = 1.0 / (p + b)
-    bp = joseph.back(sxs, sxe, q, geom, mode="tof_lm", tof=tof, tof_bin=stb, threads=threads)
+    bp = joseph.back(sxs, sxe, q, geom, mode="tof_lm", tof=tof, tof_bin=stb, threads=threads, sigma=ssg)
     if res:
         bp = resolution.gauss3d(bp, geom, fwhm_mm, truncate, adjoint=True)
     s = np.asarray(sens, dtype=np.float64) / n_sub
@@ -47,14 +48,14 @@ def lm_osem_subset_update(x, xs, xe, tof_bin, geom, tof, sens, b, m, n_sub, thre
 
 
 def lm_osem(xs, xe, tof_bin, geom, tof, sens, b, n_iter, n_sub, threads=1, x0=None, fwhm_mm=0.0,
-            truncate=4.0):
+            truncate=4.0, sigma=None):
     """Full TOF listmode OSEM: x0 = 1 on voxels with s > 0 (else 0)."""
     sens = np.asarray(sens, dtype=np.float64)
     x = (sens > 0).astype(np.float64) if x0 is None else np.asarray(x0, dtype=np.float64).copy()
     for _ in range(n_iter):
         for m in range(n_sub):
             x = lm_osem_subset_update(x, xs, xe, tof_bin, geom, tof, sens, b, m, n_sub, threads, fwhm_mm,
-                                      truncate)
+                                      truncate, sigma)
     return x
 
 

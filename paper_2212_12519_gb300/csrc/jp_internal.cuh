@@ -41,10 +41,14 @@ struct DevGeom {
 };
 
 struct DevTof {
+  const float* user;  // tabulated kernel (device) or nullptr for the Gaussian
+  int nodes;       // table nodes over [-R, R]: the shared-memory table or `user`
+  float inv_h;     // (nodes - 1) / (2 R)
   float width;     // TOF bin width w
   float half;      // w / 2
   float k;         // 1 / (sqrt2 sigma)
-  float R;         // n_sigmas * sigma + w / 2 (support half-width)
+  float ns;        // n_sigmas (per-event sigma: R_e = ns sigma_e + w / 2)
+  float R;         // support half-width: n_sigmas * sigma + w / 2, or the table's
   float R_over_w;  // R / w
   float inv_w;     // 1 / w
   float hbin;      // (N - 1) / 2
@@ -244,8 +248,20 @@ __device__ __forceinline__ void scatter_add(float* img, const Ray& r, const Corn
   if (q.m11) atomicAdd(img + q.idx + r.sb + r.sc, q.w11 * val);
 }
 
+// tabulated kernel at dist, linear interpolation between the nodes (the
+// same formula as the shared-memory table lookup)
+__device__ __forceinline__ float user_g(float dist, const DevTof& t) {
+  float x = (dist + t.R) * t.inv_h;
+  x = fminf(fmaxf(x, 0.f), (float)(t.nodes - 1));
+  const int ix = min((int)x, t.nodes - 2);
+  const float fr = x - (float)ix;
+  const float g0 = __ldg(t.user + ix);
+  return fmaf(fr, __ldg(t.user + ix + 1) - g0, g0);
+}
+
 // TOF weight of one bin, no truncation test (the caller decides the window)
 __device__ __forceinline__ float tof_g(float dist, const DevTof& t) {
+  if (t.user) return user_g(dist, t);
   return 0.5f * (erff((dist + t.half) * t.k) - erff((dist - t.half) * t.k));
 }
 
@@ -326,4 +342,6 @@ struct jp_plan_s {
   int32_t* axis_used;     // [frame_capacity * 3]: frame f has LORs with principal axis a
   uint32_t* work_counter; // chunk counter of the persistent projection kernels
   float* fold_img;        // [nvox] folded back projection of an OSEM subset (interleaved plans only)
+  float* sig_binned;      // [capacity] per-event TOF sigma in binned order (allocated on first use)
+  bool has_sigma;         // sig_binned is current for the bound LORs
 };

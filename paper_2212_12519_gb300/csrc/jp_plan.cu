@@ -271,6 +271,8 @@ int bind(jp_plan p, const float* xs, const float* xe, const int16_t* tof_bin, co
   if (n > p->capacity || n_frames > p->frame_capacity)
     return fail(JP_ERR_ARG, "rebind exceeds the plan's capacity");
   if (n > 0 && (!xs || !xe)) return fail(JP_ERR_ARG, "xstart/xend is NULL");
+  // a new binding invalidates the per-event sigma gathered for the old one
+  p->has_sigma = false;
   if (!aligned(xs, 4) || !aligned(xe, 4) || !aligned(tof_bin, 2) || !aligned(delta, 4))
     return fail(JP_ERR_ALIGN, "misaligned LOR arrays");
   p->has_tof_bin = tof_bin != nullptr;
@@ -352,6 +354,7 @@ void free_plan(jp_plan p) {
   cudaFree(p->axis_used);
   cudaFree(p->work_counter);
   cudaFree(p->fold_img);
+  cudaFree(p->sig_binned);
   delete p;
 }
 
@@ -465,6 +468,48 @@ extern "C" int jp_plan_create(jp_plan* out, const float* xs, const float* xe,
   }
   int64_t off[2] = {0, n_lor};
   return jp_plan_create_batch(out, xs, xe, tof_bin, delta, off, 1, g, opts, stream);
+}
+
+namespace jp {
+namespace {
+// sig_binned[i] = sigma[caller index of binned LOR i]
+__global__ void sigma_gather_kernel(const float4* __restrict__ lor, const int32_t* __restrict__ perm, int perm_in_rec,
+                                    const float* __restrict__ sigma, float* __restrict__ out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = perm_in_rec ? (int64_t)__float_as_int(lor[2 * i].w) : (int64_t)perm[i];
+    out[i] = __ldg(sigma + j);
+  }
+}
+}  // namespace
+}  // namespace jp
+
+extern "C" int jp_plan_set_event_sigma(jp_plan p, const float* sigma, void* stream) {
+  using namespace jp;
+  clear_error();
+  if (!p) return fail(JP_ERR_ARG, "plan is NULL");
+  if (!sigma) {
+    p->has_sigma = false;
+    return JP_OK;
+  }
+  if (!aligned(sigma, 4)) return fail(JP_ERR_ALIGN, "sigma must be 4-byte aligned");
+  if (!p->sig_binned) {
+    cudaError_t e = cudaMalloc(&p->sig_binned, sizeof(float) * (size_t)std::max<int64_t>(p->capacity, 1));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      p->sig_binned = nullptr;
+      return fail(e == cudaErrorMemoryAllocation ? JP_ERR_NOMEM : JP_ERR_CUDA,
+                  std::string("per-event sigma allocation: ") + cudaGetErrorString(e));
+    }
+  }
+  if (p->n > 0) {
+    const int64_t blocks = std::min<int64_t>((p->n + 255) / 256, (int64_t)sm_count() * 8);
+    sigma_gather_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(p->lor, p->perm, p->has_delta ? 0 : 1,
+                                                                           sigma, p->sig_binned, p->n);
+    count_launch();
+    JP_TRY_CUDA(cudaGetLastError());
+  }
+  p->has_sigma = true;
+  return JP_OK;
 }
 
 extern "C" int jp_plan_rebind(jp_plan p, const float* xs, const float* xe, const int16_t* tof_bin,

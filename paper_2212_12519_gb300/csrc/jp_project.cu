@@ -48,14 +48,33 @@ int make_geom(const jp_image_geom* g, DevGeom* out) {
 int make_tof(const jp_tof* t, bool sino, DevTof* out) {
   if (!t) return fail(JP_ERR_ARG, "TOF parameters are NULL");
   if (!(t->bin_width > 0.f) || !isfinite(t->bin_width)) return fail(JP_ERR_ARG, "TOF bin width must be finite and > 0");
-  if (!(t->sigma > 0.f) || !isfinite(t->sigma)) return fail(JP_ERR_ARG, "TOF sigma must be finite and > 0");
-  if (!(t->n_sigmas > 0.f) || !isfinite(t->n_sigmas)) return fail(JP_ERR_ARG, "TOF n_sigmas must be finite and > 0");
+  if (t->kernel) {
+    if (t->kernel_nodes < 2 || t->kernel_nodes > JP_TOF_TABLE)
+      return fail(JP_ERR_ARG, "TOF kernel_nodes must be in 2..JP_TOF_TABLE");
+    if (!(t->kernel_half_width > 0.f) || !isfinite(t->kernel_half_width))
+      return fail(JP_ERR_ARG, "TOF kernel_half_width must be finite and > 0");
+    if (!aligned(t->kernel, 4)) return fail(JP_ERR_ALIGN, "TOF kernel table must be 4-byte aligned");
+  } else {
+    if (!(t->sigma > 0.f) || !isfinite(t->sigma)) return fail(JP_ERR_ARG, "TOF sigma must be finite and > 0");
+    if (!(t->n_sigmas > 0.f) || !isfinite(t->n_sigmas)) return fail(JP_ERR_ARG, "TOF n_sigmas must be finite and > 0");
+  }
   if (sino && (t->n_bins < 1 || t->n_bins > JP_MAX_TOF_BINS))
     return fail(JP_ERR_ARG, "TOF n_bins must be in 1..JP_MAX_TOF_BINS");
   out->width = t->bin_width;
   out->half = 0.5f * t->bin_width;
-  out->k = 1.0f / (1.41421356237309515f * t->sigma);
-  out->R = t->n_sigmas * t->sigma + 0.5f * t->bin_width;
+  out->user = t->kernel;
+  if (t->kernel) {
+    out->k = 0.f;
+    out->ns = 0.f;
+    out->R = t->kernel_half_width;
+    out->nodes = t->kernel_nodes;
+  } else {
+    out->k = 1.0f / (1.41421356237309515f * t->sigma);
+    out->R = t->n_sigmas * t->sigma + 0.5f * t->bin_width;
+    out->ns = t->n_sigmas;
+    out->nodes = JP_TOF_TABLE;
+  }
+  out->inv_h = (float)(out->nodes - 1) / (2.f * out->R);
   out->R_over_w = out->R / t->bin_width;
   out->inv_w = 1.0f / t->bin_width;
   out->nbins = sino ? t->n_bins : 1;
@@ -69,6 +88,8 @@ constexpr int kMaxBlock = 512;
 constexpr int kLut = JP_TOF_TABLE;  // table nodes over [-R, R]
 
 struct ProjParams {
+  // per-event TOF sigma in binned order (listmode), or nullptr
+  const float* sig;
   // planned source
   const float4* lor;
   const int32_t* perm;
@@ -123,28 +144,43 @@ __device__ __forceinline__ int frame_of(const int64_t* __restrict__ off, int n_f
 // The nodes are exact erf differences; linear interpolation between them is
 // the table method of the TOF kernel mentioned in the paper's Sec. 4.
 // ---------------------------------------------------------------------------
+// With a tabulated kernel (T.user) the table holds the caller's T.nodes
+// nodes instead.
 __device__ void build_lut(float2* lut, const DevTof& T) {
-  const float h = 2.f * T.R / (float)(kLut - 1);
-  for (int e = threadIdx.x; e < kLut - 1; e += blockDim.x) {
+  if (T.user) {
+    for (int e = threadIdx.x; e < T.nodes - 1; e += blockDim.x) {
+      const float g0 = __ldg(T.user + e);
+      lut[e] = make_float2(g0, __ldg(T.user + e + 1) - g0);
+    }
+    return;
+  }
+  const float h = 2.f * T.R / (float)(T.nodes - 1);
+  for (int e = threadIdx.x; e < T.nodes - 1; e += blockDim.x) {
     float g0 = tof_g(fmaf((float)e, h, -T.R), T);
     float g1 = tof_g(fmaf((float)(e + 1), h, -T.R), T);
     lut[e] = make_float2(g0, g1 - g0);
   }
 }
 
-__device__ __forceinline__ float lut_g(const float2* lut, float dist, float R, float inv_h) {
-  float x = (dist + R) * inv_h;
-  x = fminf(fmaxf(x, 0.f), (float)(kLut - 1) - 1e-3f);
-  int ix = (int)x;
+// x is clamped to [0, nodes - 1] and the last interval also serves x =
+// nodes - 1 (fraction 1), so the end nodes are reproduced exactly
+__device__ __forceinline__ float lut_g(const float2* lut, float dist, const DevTof& T) {
+  float x = (dist + T.R) * T.inv_h;
+  x = fminf(fmaxf(x, 0.f), (float)(T.nodes - 1));
+  const int ix = min((int)x, T.nodes - 2);
   float fr = x - (float)ix;
   float2 e = lut[ix];
   return fmaf(fr, e.y, e.x);
 }
 
+// k_e: 1 / (sqrt2 sigma) of the LOR (its own sigma with per-event TOF
+// resolution, else T.k); the shared-memory table holds T's sigma only, so a
+// per-event sigma takes the exact path
 template <bool LUT>
-__device__ __forceinline__ float tof_weight(const float2* lut, float dist, const DevTof& T, float inv_h) {
-  if (LUT) return lut_g(lut, dist, T.R, inv_h);
-  return tof_g(dist, T);
+__device__ __forceinline__ float tof_weight(const float2* lut, float dist, const DevTof& T, float k_e) {
+  if (LUT) return lut_g(lut, dist, T);
+  if (T.user) return user_g(dist, T);
+  return 0.5f * (erff((dist + T.half) * k_e) - erff((dist - T.half) * k_e));
 }
 
 __device__ __forceinline__ bool slot_axis_used(const int32_t* used, int slot, int a, int shared, int n_frames) {
@@ -152,6 +188,21 @@ __device__ __forceinline__ bool slot_axis_used(const int32_t* used, int slot, in
   for (int f = 0; f < n_frames; ++f)
     if (__ldg(used + 3 * f + a)) return true;
   return false;
+}
+
+// TOF resolution of binned listmode LOR i: k = 1 / (sqrt2 sigma) and the
+// support half-width R, from its own sigma when the plan has per-event sigma
+// (a value <= 0 keeps the scalar one; a tabulated kernel ignores sigma)
+__device__ __forceinline__ void event_tof(const ProjParams& p, int64_t i, float& k, float& R) {
+  k = p.tof.k;
+  R = p.tof.R;
+  if (p.sig && !p.tof.user) {
+    const float s = __ldg(p.sig + i);
+    if (s > 0.f) {
+      k = 1.0f / (1.41421356237309515f * s);
+      R = fmaf(p.tof.ns, s, p.tof.half);
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -168,7 +219,6 @@ __global__ void __launch_bounds__(kMaxBlock) planned_kernel(const ProjParams p) 
     build_lut(lut, T);
     __syncthreads();
   }
-  const float inv_h = (MODE != 0) ? (float)(kLut - 1) / (2.f * T.R) : 0.f;
   const int N = T.nbins;
   __shared__ unsigned int tile_s;
   for (;;) {
@@ -190,10 +240,13 @@ __global__ void __launch_bounds__(kMaxBlock) planned_kernel(const ProjParams p) 
     Ray r;
     bool live = ray_setup(xs, xe, p.g, r);
     float d0 = 0.f;  // tau(kc) - c  (listmode)
+    float ke = T.k;
     if (MODE == 2 && live) {
+      float Re;
+      event_tof(p, i, ke, Re);
       const float c = (float)tbin * T.width + delta;
       d0 = r.tc - c;
-      const float t1 = (-T.R - d0) / r.dt, t2 = (T.R - d0) / r.dt;
+      const float t1 = (-Re - d0) / r.dt, t2 = (Re - d0) / r.dt;
       const float lo = fmaxf(ceilf(r.kc + fminf(t1, t2)), (float)r.k0);
       const float hi = fminf(floorf(r.kc + fmaxf(t1, t2)), (float)r.k1);
       r.k0 = (int)lo;
@@ -227,7 +280,7 @@ __global__ void __launch_bounds__(kMaxBlock) planned_kernel(const ProjParams p) 
           if (MODE == 0) {
             sum += s;
           } else if (MODE == 2) {
-            sum = fmaf(tof_weight<LUT>(lut, fmaf(kk, r.dt, d0), T, inv_h), s, sum);
+            sum = fmaf(tof_weight<LUT>(lut, fmaf(kk, r.dt, d0), T, ke), s, sum);
           } else {
             if (s == 0.f) continue;
             const float tau = fmaf(kk, r.dt, r.tc);
@@ -239,7 +292,7 @@ __global__ void __launch_bounds__(kMaxBlock) planned_kernel(const ProjParams p) 
             if (LUT) {
               for (int t = t0; t <= t1; ++t) {
                 const float dist = fmaf(-(float)(t - t0), T.width, dlo);
-                acc[t * blockDim.x] = fmaf(lut_g(lut, dist, T.R, inv_h), s, acc[t * blockDim.x]);
+                acc[t * blockDim.x] = fmaf(lut_g(lut, dist, T), s, acc[t * blockDim.x]);
               }
             } else {
               float e_hi = erff((dlo + T.half) * T.k);
@@ -283,7 +336,7 @@ __global__ void __launch_bounds__(kMaxBlock) planned_kernel(const ProjParams p) 
         if (MODE == 0) {
           coef = val;
         } else if (MODE == 2) {
-          coef = tof_weight<LUT>(lut, fmaf(kk, r.dt, d0), T, inv_h) * val;
+          coef = tof_weight<LUT>(lut, fmaf(kk, r.dt, d0), T, ke) * val;
         } else {
           const float tau = fmaf(kk, r.dt, r.tc);
           const float x = (tau - delta) * T.inv_w + T.hbin;
@@ -295,7 +348,7 @@ __global__ void __launch_bounds__(kMaxBlock) planned_kernel(const ProjParams p) 
           if (LUT) {
             for (int t = t0; t <= t1; ++t) {
               const float dist = fmaf(-(float)(t - t0), T.width, dlo);
-              sy = fmaf(lut_g(lut, dist, T.R, inv_h), acc[t * blockDim.x], sy);
+              sy = fmaf(lut_g(lut, dist, T), acc[t * blockDim.x], sy);
             }
           } else {
             float e_hi = erff((dlo + T.half) * T.k);
@@ -347,7 +400,6 @@ __global__ void __launch_bounds__(kMaxBlock) group_kernel(const ProjParams p) {
     build_lut(lut, T);
     __syncthreads();
   }
-  const float inv_h = (MODE != 0) ? (float)(kLut - 1) / (2.f * T.R) : 0.f;
   const int N = T.nbins;
   const int lane = threadIdx.x & 31;
   const int grp = lane / G, gl = lane - grp * G;
@@ -360,7 +412,7 @@ __global__ void __launch_bounds__(kMaxBlock) group_kernel(const ProjParams p) {
     const int64_t i = base + lane;
     Ray r;
     r.k0 = 1; r.k1 = 0;
-    float d0 = 0.f, val = 0.f, delta = 0.f;
+    float d0 = 0.f, val = 0.f, delta = 0.f, ke = T.k;
     int slot = 0;
     int32_t j = 0;
     if (i < p.n) {
@@ -374,9 +426,11 @@ __global__ void __launch_bounds__(kMaxBlock) group_kernel(const ProjParams p) {
       slot = p.shared ? 0 : f;
       bool live = ray_setup(xs, xe, p.g, r);
       if (MODE == 2 && live) {
+        float Re;
+        event_tof(p, i, ke, Re);
         const float c = (float)__float_as_int(B.w) * T.width + delta;
         d0 = r.tc - c;
-        const float t1 = (-T.R - d0) / r.dt, t2 = (T.R - d0) / r.dt;
+        const float t1 = (-Re - d0) / r.dt, t2 = (Re - d0) / r.dt;
         const float lo = fmaxf(ceilf(r.kc + fminf(t1, t2)), (float)r.k0);
         const float hi = fminf(floorf(r.kc + fmaxf(t1, t2)), (float)r.k1);
         r.k0 = (int)lo;
@@ -405,10 +459,11 @@ __global__ void __launch_bounds__(kMaxBlock) group_kernel(const ProjParams p) {
       const float wc = __shfl_sync(0xffffffffu, r.wc, src);
       const float dw = __shfl_sync(0xffffffffu, r.dw, src);
       const float w0 = __shfl_sync(0xffffffffu, BACK ? val : r.w0, src);
-      float dd0 = 0.f, ddt = 0.f, dtc = 0.f, ddl = 0.f;
+      float dd0 = 0.f, ddt = 0.f, dtc = 0.f, ddl = 0.f, dke = 0.f;
       if (MODE == 2) {
         dd0 = __shfl_sync(0xffffffffu, d0, src);
         ddt = __shfl_sync(0xffffffffu, r.dt, src);
+        dke = __shfl_sync(0xffffffffu, ke, src);
       }
       if (MODE == 1) {
         ddt = __shfl_sync(0xffffffffu, r.dt, src);
@@ -437,7 +492,7 @@ __global__ void __launch_bounds__(kMaxBlock) group_kernel(const ProjParams p) {
           const float bot = fmaf(be, v.w - v.y, v.y);
           const float s = fmaf(al, bot - top, top);
           if (MODE == 0) sum += s;
-          else sum = fmaf(tof_weight<LUT>(lut, fmaf(kk, ddt, dd0), T, inv_h), s, sum);
+          else sum = fmaf(tof_weight<LUT>(lut, fmaf(kk, ddt, dd0), T, dke), s, sum);
         }
       }
       // start the group on an even plane: neighbouring lanes then cover the
@@ -452,7 +507,7 @@ __global__ void __launch_bounds__(kMaxBlock) group_kernel(const ProjParams p) {
         const int q = (((int)fu + 1) * nc2 + ((int)fw + 1)) * nap + k;
         {
           float coef = w0;
-          if (MODE == 2) coef *= tof_weight<LUT>(lut, fmaf(kk, ddt, dd0), T, inv_h);
+          if (MODE == 2) coef *= tof_weight<LUT>(lut, fmaf(kk, ddt, dd0), T, dke);
           if (MODE == 1) {
             // sum over the bins in the window of weight x sinogram value
             const float* yrow = p.proj_in + (int64_t)jj * N;
@@ -464,7 +519,7 @@ __global__ void __launch_bounds__(kMaxBlock) group_kernel(const ProjParams p) {
             float sy = 0.f;
             if (LUT) {
               for (int t = t0; t <= t1; ++t)
-                sy = fmaf(lut_g(lut, fmaf(-(float)(t - t0), T.width, dlo), T.R, inv_h), __ldg(yrow + t), sy);
+                sy = fmaf(lut_g(lut, fmaf(-(float)(t - t0), T.width, dlo), T), __ldg(yrow + t), sy);
             } else {
               float e_hi = erff((dlo + T.half) * T.k);
               for (int t = t0; t <= t1; ++t) {
@@ -510,7 +565,6 @@ __global__ void __launch_bounds__(kMaxBlock) osem_kernel(const ProjParams p) {
     build_lut(lut, T);
     __syncthreads();
   }
-  const float inv_h = (float)(kLut - 1) / (2.f * T.R);
   const int lane = threadIdx.x & 31;
   const int grp = lane / G, gl = lane - grp * G;
   const int64_t start = __ldg(p.frame_off + p.f0), end = __ldg(p.frame_off + p.f1);
@@ -531,7 +585,7 @@ __global__ void __launch_bounds__(kMaxBlock) osem_kernel(const ProjParams p) {
     const int64_t i = base + lane;
     Ray r;
     r.k0 = 1; r.k1 = 0;
-    float d0 = 0.f;
+    float d0 = 0.f, ke = T.k;
     if (lane < chunk_ev && i < end) {
       const float4 A = __ldcs(p.lor + 2 * i);
       const float4 B = __ldcs(p.lor + 2 * i + 1);
@@ -539,9 +593,11 @@ __global__ void __launch_bounds__(kMaxBlock) osem_kernel(const ProjParams p) {
       const float xe[3] = {B.x, B.y, B.z};
       bool live = ray_setup(xs, xe, p.g, r);
       if (live) {
+        float Re;
+        event_tof(p, i, ke, Re);
         const float c = (float)__float_as_int(B.w) * T.width + (p.perm_in_rec ? 0.f : A.w);
         d0 = r.tc - c;
-        const float t1 = (-T.R - d0) / r.dt, t2 = (T.R - d0) / r.dt;
+        const float t1 = (-Re - d0) / r.dt, t2 = (Re - d0) / r.dt;
         const float lo = fmaxf(ceilf(r.kc + fminf(t1, t2)), (float)r.k0);
         const float hi = fminf(floorf(r.kc + fmaxf(t1, t2)), (float)r.k1);
         r.k0 = (int)lo;
@@ -565,6 +621,7 @@ __global__ void __launch_bounds__(kMaxBlock) osem_kernel(const ProjParams p) {
       const float w0 = __shfl_sync(0xffffffffu, r.w0, src);
       const float dd0 = __shfl_sync(0xffffffffu, d0, src);
       const float ddt = __shfl_sync(0xffffffffu, r.dt, src);
+      const float dke = __shfl_sync(0xffffffffu, ke, src);
       const int na = sel3(a, p.g.n[0], p.g.n[1], p.g.n[2]);
       const int nap = sel3(a, p.ql.nap[0], p.ql.nap[1], p.ql.nap[2]);
       const int nb = (a == 0) ? p.g.n[1] : p.g.n[0];
@@ -600,7 +657,7 @@ __global__ void __launch_bounds__(kMaxBlock) osem_kernel(const ProjParams p) {
         }
         const float top = fmaf(be, v.z - v.x, v.x);
         const float bot = fmaf(be, v.w - v.y, v.y);
-        sum = fmaf(tof_weight<LUT>(lut, fmaf(kk, ddt, dd0), T, inv_h), fmaf(al, bot - top, top), sum);
+        sum = fmaf(tof_weight<LUT>(lut, fmaf(kk, ddt, dd0), T, dke), fmaf(al, bot - top, top), sum);
       }
       sum = group_sum<G>(sum);
       // ratio and back projection of it
@@ -612,7 +669,7 @@ __global__ void __launch_bounds__(kMaxBlock) osem_kernel(const ProjParams p) {
         const float w = fminf(fmaxf(fmaf(kk, dw, wc), -1.f), wb);
         const float fu = floorf(u), fw = floorf(w);
         const float al = u - fu, be = w - fw;
-        const float coef = coef0 * tof_weight<LUT>(lut, fmaf(kk, ddt, dd0), T, inv_h);
+        const float coef = coef0 * tof_weight<LUT>(lut, fmaf(kk, ddt, dd0), T, dke);
         const float ca = (1.f - al) * coef, cb = al * coef;
         if (DIRECT) {
           const int i = (int)fu, j = (int)fw;
@@ -957,6 +1014,11 @@ __global__ void __launch_bounds__(kMaxBlock) direct_kernel(const ProjParams p) {
           const int t1 = min(N - 1, (int)floorf(x + T.R_over_w));
           if (t0 > t1) continue;
           const float dlo = (tau - delta) - ((float)t0 - T.hbin) * T.width;
+          if (T.user) {
+            for (int t = t0; t <= t1; ++t)
+              acc[t * blockDim.x] += user_g(fmaf(-(float)(t - t0), T.width, dlo), T) * s;
+            continue;
+          }
           float e_hi = erff((dlo + T.half) * T.k);
           for (int t = t0; t <= t1; ++t) {
             const float dist = fmaf(-(float)(t - t0), T.width, dlo);
@@ -1003,13 +1065,18 @@ __global__ void __launch_bounds__(kMaxBlock) direct_kernel(const ProjParams p) {
         const int t1 = min(N - 1, (int)floorf(x + T.R_over_w));
         if (t0 > t1) continue;
         const float dlo = (tau - delta) - ((float)t0 - T.hbin) * T.width;
-        float e_hi = erff((dlo + T.half) * T.k);
         float sy = 0.f;
-        for (int t = t0; t <= t1; ++t) {
-          const float dist = fmaf(-(float)(t - t0), T.width, dlo);
-          const float e_lo = erff((dist - T.half) * T.k);
-          sy += 0.5f * (e_hi - e_lo) * acc[t * blockDim.x];
-          e_hi = e_lo;
+        if (T.user) {
+          for (int t = t0; t <= t1; ++t)
+            sy += user_g(fmaf(-(float)(t - t0), T.width, dlo), T) * acc[t * blockDim.x];
+        } else {
+          float e_hi = erff((dlo + T.half) * T.k);
+          for (int t = t0; t <= t1; ++t) {
+            const float dist = fmaf(-(float)(t - t0), T.width, dlo);
+            const float e_lo = erff((dist - T.half) * T.k);
+            sy += 0.5f * (e_hi - e_lo) * acc[t * blockDim.x];
+            e_hi = e_lo;
+          }
         }
         coef = sy * val;
       }
@@ -1216,7 +1283,11 @@ int planned(jp_plan pl, int mode, bool back, const float* in, float* out, int64_
   if (back) { p.proj_in = in; p.img_out = out; } else { p.img_in = in; p.proj_out = out; }
   const int slots = p.shared ? 1 : pl->n_frames;
   if (slots * 3 > 65535) return fail(JP_ERR_ARG, "too many frames with distinct images (max 21845)");
-  const bool lut = (mode != 0) && !(pl->opts.flags & JP_PLAN_TOF_EXACT);
+  if (pl->has_sigma && mode == 2) p.sig = pl->sig_binned;
+  if (pl->has_sigma && mode == 1) return fail(JP_ERR_STATE, "per-event sigma applies to TOF listmode only");
+  // a tabulated kernel always goes through the shared-memory table; a
+  // per-event sigma takes the exact path (the table holds one sigma)
+  const bool lut = (mode != 0) && ((!(pl->opts.flags & JP_PLAN_TOF_EXACT) && !p.sig) || p.tof.user);
   const int block = pick_block(pl->opts.block, mode, p.tof, lut);
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t max_quad = std::max(std::max(p.ql.size[0], p.ql.size[1]), p.ql.size[2]);
@@ -1310,9 +1381,11 @@ __global__ void count_kernel(const ProjParams p, unsigned long long* out) {
     Ray r;
     bool live = ray_setup(xs, xe, p.g, r);
     if (live && MODE == 2) {
+      float ke, Re;
+      event_tof(p, i, ke, Re);
       const float c = (float)__float_as_int(B.w) * p.tof.width + (p.perm_in_rec ? 0.f : A.w);
       const float d0 = r.tc - c;
-      const float t1 = (-p.tof.R - d0) / r.dt, t2 = (p.tof.R - d0) / r.dt;
+      const float t1 = (-Re - d0) / r.dt, t2 = (Re - d0) / r.dt;
       const float lo = fmaxf(ceilf(r.kc + fminf(t1, t2)), (float)r.k0);
       const float hi = fminf(floorf(r.kc + fmaxf(t1, t2)), (float)r.k1);
       r.k0 = (int)lo;
@@ -1347,6 +1420,7 @@ extern "C" int jp_count_samples(jp_plan pl, int32_t mode, const jp_tof* t, uint6
   p.lor = pl->lor;
   p.n = pl->n;
   p.perm_in_rec = pl->has_delta ? 0 : 1;
+  if (mode == 2 && pl->has_sigma) p.sig = pl->sig_binned;
   cudaStream_t st = (cudaStream_t)stream;
   JP_TRY_CUDA(cudaMemsetAsync(out, 0, sizeof(uint64_t), st));
   if (p.n == 0) return JP_OK;
@@ -1439,6 +1513,7 @@ int osem_subset(jp_plan pl, int32_t f0, int32_t f1, float* x, const float* sens,
   p.sens_scale = sens_scale;
   p.counter = pl->work_counter;
   p.perm_in_rec = pl->has_delta ? 0 : 1;
+  p.sig = pl->has_sigma ? pl->sig_binned : nullptr;
   // back-projection image of the direct path (and of the quads path's fold)
   float* bp_img = res ? wt : pl->fold_img;
   const int64_t max_quad = std::max(std::max(p.ql.size[0], p.ql.size[1]), p.ql.size[2]);
@@ -1462,7 +1537,7 @@ int osem_subset(jp_plan pl, int32_t f0, int32_t f1, float* x, const float* sens,
     JP_TRY_CUDA(cudaGetLastError());
   }
   if (pl->capacity > 0) {
-    const bool lut = !(pl->opts.flags & JP_PLAN_TOF_EXACT);
+    const bool lut = (!(pl->opts.flags & JP_PLAN_TOF_EXACT) && !p.sig) || p.tof.user;
     int lpw = pl->opts.lors_per_warp;
     if (lpw != 1 && lpw != 2) lpw = 4;
     const int block = std::min(pl->opts.block, kMaxBlock);

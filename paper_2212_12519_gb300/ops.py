@@ -41,7 +41,8 @@ class ImageGeomC(ctypes.Structure):
 
 
 class TofC(ctypes.Structure):
-    _fields_ = [("bin_width", F32), ("sigma", F32), ("n_sigmas", F32), ("n_bins", I32)]
+    _fields_ = [("bin_width", F32), ("sigma", F32), ("n_sigmas", F32), ("n_bins", I32),
+                ("kernel", P), ("kernel_nodes", I32), ("kernel_half_width", F32)]
 
 
 class ResolutionC(ctypes.Structure):
@@ -62,6 +63,7 @@ _SIGS = {
     "jp_plan_create": [ctypes.POINTER(P), P, P, P, P, I64, P, P, P],
     "jp_plan_rebind": [P, P, P, P, P, P, I32, P],
     "jp_plan_destroy": [P],
+    "jp_plan_set_event_sigma": [P, P, P],
     "jp_plan_info": [P, P, P, P, P],
     "jp_fwd": [P, P, I64, P, P],
     "jp_back": [P, P, P, I64, P],
@@ -160,8 +162,26 @@ def resolution(fwhm_mm, truncate: float = 4.0) -> ResolutionC:
     return r
 
 
+_kernel_tables: dict = {}
+
+
+def _kernel_table(values, device) -> torch.Tensor:
+    """Device copy of a tabulated TOF kernel, made once per table and device."""
+    key = (tuple(values), str(device))
+    t = _kernel_tables.get(key)
+    if t is None:
+        t = torch.tensor(values, dtype=torch.float32, device=device)
+        _kernel_tables[key] = t
+    return t
+
+
 def tof_params(tof) -> TofC:
-    return TofC(float(tof.bin_width), float(tof.sigma), float(tof.n_sigmas), int(tof.n_bins))
+    kernel = getattr(tof, "kernel", None)
+    if kernel is None:
+        return TofC(float(tof.bin_width), float(tof.sigma), float(tof.n_sigmas), int(tof.n_bins), None, 0, 0.0)
+    tab = _kernel_table(kernel, torch.device("cuda", torch.cuda.current_device()))
+    return TofC(float(tof.bin_width), float(tof.sigma), float(tof.n_sigmas), int(tof.n_bins),
+                P(tab.data_ptr()), int(tab.numel()), float(tof.kernel_half_width))
 
 
 def _lors(xs, xe):
@@ -243,6 +263,15 @@ def jp_plan_create_subsets(xs, xe, geom, n_subsets, tof_bin=None, delta=None, st
     plan = jp_plan_create_batch(xs, xe, geom, off, tof_bin, delta, stream, interleaved=True, **opts)
     plan.frame_offsets = [sum(n // n_subsets + (1 if f < n % n_subsets else 0) for f in range(m))
                           for m in range(n_subsets + 1)]
+    return plan
+
+
+def jp_plan_set_event_sigma(plan: Plan, sigma, stream=None):
+    """Per-event TOF sigma (mm, float32 [n], caller order) for the plan's
+    bound listmode events; None clears it.  Rebinding clears it too."""
+    if sigma is not None and sigma.numel() != plan.n:
+        raise ValueError("sigma must hold one value per bound event")
+    _check(load().jp_plan_set_event_sigma(plan.handle, _ptr(sigma, torch.float32, "sigma"), _stream(stream)))
     return plan
 
 

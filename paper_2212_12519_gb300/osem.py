@@ -82,6 +82,7 @@ class FrameSpec:
     n_sub: int = 8
     fwhm_mm: float = 0.0    # resolution model (0: none); sens must then be H^T A^T 1
     path: str = "auto"      # subset update path: "auto", "quads" or "direct"
+    sigma: Optional[torch.Tensor] = None  # per-event TOF sigma (mm), caller order
 
 
 class LMOSEMFrame:
@@ -110,6 +111,8 @@ class LMOSEMFrame:
                 plan.frame_offsets = [sum(n // spec.n_sub + (1 if f < n % spec.n_sub else 0) for f in range(m))
                                       for m in range(spec.n_sub + 1)]
                 self.plan = plan
+            if spec.sigma is not None:
+                ops.jp_plan_set_event_sigma(self.plan, spec.sigma)
             self.x = torch.empty(spec.geom.shape, dtype=torch.float32, device=spec.xs.device)
             self.work = (torch.empty((2,) + tuple(spec.geom.shape), dtype=torch.float32, device=spec.xs.device)
                          if spec.fwhm_mm > 0 else None)

@@ -61,17 +61,32 @@ class ImageGeom:
 @dataclass(frozen=True)
 class TofParams:
     """TOF kernel parameters (Sec. 2.1 and 2.6): bin width (mm), Gaussian
-    sigma (mm), truncation in sigmas, number of sinogram TOF bins."""
+    sigma (mm), truncation in sigmas, number of sinogram TOF bins.
+
+    ``kernel`` optionally replaces the Gaussian by a tabulated bin response
+    (Sec. 5: a 1D lookup table for non-Gaussian TOF kernels): the values at
+    the distances -h + e 2h / (len - 1) from the bin centre, h =
+    ``kernel_half_width``, linearly interpolated, 0 beyond h."""
 
     bin_width: float
     sigma: float
     n_sigmas: float
     n_bins: int
+    kernel: Optional[Tuple[float, ...]] = None
+    kernel_half_width: float = 0.0
 
     @staticmethod
     def from_fwhm(bin_width: float, fwhm: float, n_sigmas: float, n_bins: int) -> "TofParams":
         return TofParams(float(bin_width), float(fwhm / (2.0 * math.sqrt(2.0 * math.log(2.0)))),
                          float(n_sigmas), int(n_bins))
+
+    @staticmethod
+    def tabulated(bin_width: float, n_bins: int, values: Sequence[float], half_width: float) -> "TofParams":
+        """A non-Gaussian TOF kernel given by its table (sigma, n_sigmas unused)."""
+        vals = tuple(float(v) for v in values)
+        if len(vals) < 2:
+            raise ValueError("a TOF kernel table needs at least 2 nodes")
+        return TofParams(float(bin_width), 0.0, 0.0, int(n_bins), vals, float(half_width))
 
 
 @dataclass(frozen=True)
