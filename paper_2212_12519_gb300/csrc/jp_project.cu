@@ -145,13 +145,15 @@ __device__ __forceinline__ int frame_of(const int64_t* __restrict__ off, int n_f
 // the table method of the TOF kernel mentioned in the paper's Sec. 4.
 // ---------------------------------------------------------------------------
 // With a tabulated kernel (T.user) the table holds the caller's T.nodes
-// nodes instead.
+// nodes instead.  Entry nodes - 1 holds (g_last, 0), so a coordinate that
+// rounds to a hair above the last node needs no clamp of the fraction.
 __device__ void build_lut(float2* lut, const DevTof& T) {
   if (T.user) {
     for (int e = threadIdx.x; e < T.nodes - 1; e += blockDim.x) {
       const float g0 = __ldg(T.user + e);
       lut[e] = make_float2(g0, __ldg(T.user + e + 1) - g0);
     }
+    if (threadIdx.x == 0) lut[T.nodes - 1] = make_float2(__ldg(T.user + T.nodes - 1), 0.f);
     return;
   }
   const float h = 2.f * T.R / (float)(T.nodes - 1);
@@ -160,6 +162,16 @@ __device__ void build_lut(float2* lut, const DevTof& T) {
     float g1 = tof_g(fmaf((float)(e + 1), h, -T.R), T);
     lut[e] = make_float2(g0, g1 - g0);
   }
+  if (threadIdx.x == 0) lut[T.nodes - 1] = make_float2(tof_g(T.R, T), 0.f);
+}
+
+// table value at the table coordinate xl = (dist + R) / h of a bin inside
+// the support (so xl is in [0, nodes - 1] up to rounding); the index clamp
+// only keeps the shared-memory read in bounds for any input
+__device__ __forceinline__ float lut_at(const float2* lut, float xl, int last) {
+  const int ix = min(max((int)xl, 0), last);
+  const float2 e = lut[ix];
+  return fmaf(xl - (float)ix, e.y, e.x);
 }
 
 // x is clamped to [0, nodes - 1] and the last interval also serves x =
@@ -290,10 +302,11 @@ __global__ void __launch_bounds__(kMaxBlock) planned_kernel(const ProjParams p) 
             if (t0 > t1) continue;
             const float dlo = (tau - delta) - ((float)t0 - T.hbin) * T.width;
             if (LUT) {
-              for (int t = t0; t <= t1; ++t) {
-                const float dist = fmaf(-(float)(t - t0), T.width, dlo);
-                acc[t * blockDim.x] = fmaf(lut_g(lut, dist, T), s, acc[t * blockDim.x]);
-              }
+              // table coordinate of bin t0, stepping down by w / h per bin
+              const float xl0 = (dlo + T.R) * T.inv_h, step = T.width * T.inv_h;
+              float* a = acc + t0 * blockDim.x;
+              for (int t = 0; t <= t1 - t0; ++t, a += blockDim.x)
+                *a = fmaf(lut_at(lut, fmaf(-(float)t, step, xl0), T.nodes - 1), s, *a);
             } else {
               float e_hi = erff((dlo + T.half) * T.k);
               for (int t = t0; t <= t1; ++t) {
@@ -346,10 +359,10 @@ __global__ void __launch_bounds__(kMaxBlock) planned_kernel(const ProjParams p) 
           const float dlo = (tau - delta) - ((float)t0 - T.hbin) * T.width;
           float sy = 0.f;
           if (LUT) {
-            for (int t = t0; t <= t1; ++t) {
-              const float dist = fmaf(-(float)(t - t0), T.width, dlo);
-              sy = fmaf(lut_g(lut, dist, T), acc[t * blockDim.x], sy);
-            }
+            const float xl0 = (dlo + T.R) * T.inv_h, step = T.width * T.inv_h;
+            const float* a = acc + t0 * blockDim.x;
+            for (int t = 0; t <= t1 - t0; ++t, a += blockDim.x)
+              sy = fmaf(lut_at(lut, fmaf(-(float)t, step, xl0), T.nodes - 1), *a, sy);
           } else {
             float e_hi = erff((dlo + T.half) * T.k);
             for (int t = t0; t <= t1; ++t) {
@@ -518,8 +531,9 @@ __global__ void __launch_bounds__(kMaxBlock) group_kernel(const ProjParams p) {
             const float dlo = (tau - ddl) - ((float)t0 - T.hbin) * T.width;
             float sy = 0.f;
             if (LUT) {
+              const float xl0 = (dlo + T.R) * T.inv_h, step = T.width * T.inv_h;
               for (int t = t0; t <= t1; ++t)
-                sy = fmaf(lut_g(lut, fmaf(-(float)(t - t0), T.width, dlo), T), __ldg(yrow + t), sy);
+                sy = fmaf(lut_at(lut, fmaf(-(float)(t - t0), step, xl0), T.nodes - 1), __ldg(yrow + t), sy);
             } else {
               float e_hi = erff((dlo + T.half) * T.k);
               for (int t = t0; t <= t1; ++t) {
