@@ -53,6 +53,13 @@ struct DevTof {
   float inv_w;     // 1 / w
   float hbin;      // (N - 1) / 2
   int nbins;       // N
+  // bin-aligned table of the sinogram kernels (Gaussian only): node spacing
+  // h = w / m, nodes at -Rp + e h with Rp = c h >= R, so the coordinates of
+  // one sample's bins differ by exactly m nodes (m = 0: not used)
+  int m;
+  int nodes_a;     // 2 c + 1
+  float Rp;        // c h
+  float inv_hp;    // 1 / h
 };
 
 int make_geom(const jp_image_geom* g, DevGeom* out);

@@ -75,6 +75,28 @@ int make_tof(const jp_tof* t, bool sino, DevTof* out) {
     out->nodes = JP_TOF_TABLE;
   }
   out->inv_h = (float)(out->nodes - 1) / (2.f * out->R);
+  // bin-aligned sinogram table: the largest m with 2 ceil(R m / w) + 1 <=
+  // JP_TOF_TABLE nodes (at least 4 nodes per bin, else not used)
+  out->m = 0;
+  out->nodes_a = 0;
+  out->Rp = 0.f;
+  out->inv_hp = 0.f;
+  if (!t->kernel) {
+    const double cmax = (double)((JP_TOF_TABLE - 1) / 2);
+    const double ratio = (double)out->R / (double)t->bin_width;
+    const int m = (int)floor(cmax / ratio);
+    if (m >= 4) {
+      const double h = (double)t->bin_width / m;
+      int c = (int)ceil((double)out->R / h);
+      if (2 * c + 1 > JP_TOF_TABLE) c = (JP_TOF_TABLE - 1) / 2;
+      if ((double)c * h >= (double)out->R) {
+        out->m = m;
+        out->nodes_a = 2 * c + 1;
+        out->Rp = (float)(c * h);
+        out->inv_hp = (float)(1.0 / h);
+      }
+    }
+  }
   out->R_over_w = out->R / t->bin_width;
   out->inv_w = 1.0f / t->bin_width;
   out->nbins = sino ? t->n_bins : 1;
@@ -165,6 +187,19 @@ __device__ void build_lut(float2* lut, const DevTof& T) {
   if (threadIdx.x == 0) lut[T.nodes - 1] = make_float2(tof_g(T.R, T), 0.f);
 }
 
+// bin-aligned table (T.m > 0): node e at -Rp + e h, h = w / m, untruncated
+// erf differences (the bin selection applies the truncation), last entry
+// (g_last, 0)
+__device__ void build_lut_aligned(float2* lut, const DevTof& T) {
+  const float h = T.width / (float)T.m;
+  for (int e = threadIdx.x; e < T.nodes_a - 1; e += blockDim.x) {
+    const float g0 = tof_g(fmaf((float)e, h, -T.Rp), T);
+    const float g1 = tof_g(fmaf((float)(e + 1), h, -T.Rp), T);
+    lut[e] = make_float2(g0, g1 - g0);
+  }
+  if (threadIdx.x == 0) lut[T.nodes_a - 1] = make_float2(tof_g(T.Rp, T), 0.f);
+}
+
 // table value at the table coordinate xl = (dist + R) / h of a bin inside
 // the support (so xl is in [0, nodes - 1] up to rounding); the index clamp
 // only keeps the shared-memory read in bounds for any input
@@ -228,7 +263,10 @@ __global__ void __launch_bounds__(kMaxBlock) planned_kernel(const ProjParams p) 
   float* acc = accbase + threadIdx.x;  // TOF sinogram: acc[t * blockDim.x]
   const DevTof& T = p.tof;
   if (MODE != 0 && LUT) {
-    build_lut(lut, T);
+    if (MODE == 1 && T.m > 0)
+      build_lut_aligned(lut, T);
+    else
+      build_lut(lut, T);
     __syncthreads();
   }
   const int N = T.nbins;
@@ -301,7 +339,18 @@ __global__ void __launch_bounds__(kMaxBlock) planned_kernel(const ProjParams p) 
             const int t1 = min(N - 1, (int)floorf(x + T.R_over_w));
             if (t0 > t1) continue;
             const float dlo = (tau - delta) - ((float)t0 - T.hbin) * T.width;
-            if (LUT) {
+            if (LUT && T.m > 0) {
+              // bin-aligned table: one fraction for all of the sample's bins,
+              // the node index steps down by m per bin
+              const float xl0 = (dlo + T.Rp) * T.inv_hp;
+              const int ix0 = min(max((int)xl0, 0), T.nodes_a - 1);
+              const float fr = xl0 - (float)ix0;
+              float* a = acc + t0 * blockDim.x;
+              for (int t = 0, ix = ix0; t <= t1 - t0; ++t, ix -= T.m, a += blockDim.x) {
+                const float2 e = lut[max(ix, 0)];
+                *a = fmaf(fmaf(fr, e.y, e.x), s, *a);
+              }
+            } else if (LUT) {
               // table coordinate of bin t0, stepping down by w / h per bin
               const float xl0 = (dlo + T.R) * T.inv_h, step = T.width * T.inv_h;
               float* a = acc + t0 * blockDim.x;
@@ -358,7 +407,16 @@ __global__ void __launch_bounds__(kMaxBlock) planned_kernel(const ProjParams p) 
           if (t0 > t1) continue;
           const float dlo = (tau - delta) - ((float)t0 - T.hbin) * T.width;
           float sy = 0.f;
-          if (LUT) {
+          if (LUT && T.m > 0) {
+            const float xl0 = (dlo + T.Rp) * T.inv_hp;
+            const int ix0 = min(max((int)xl0, 0), T.nodes_a - 1);
+            const float fr = xl0 - (float)ix0;
+            const float* a = acc + t0 * blockDim.x;
+            for (int t = 0, ix = ix0; t <= t1 - t0; ++t, ix -= T.m, a += blockDim.x) {
+              const float2 e = lut[max(ix, 0)];
+              sy = fmaf(fmaf(fr, e.y, e.x), *a, sy);
+            }
+          } else if (LUT) {
             const float xl0 = (dlo + T.R) * T.inv_h, step = T.width * T.inv_h;
             const float* a = acc + t0 * blockDim.x;
             for (int t = 0; t <= t1 - t0; ++t, a += blockDim.x)
@@ -410,7 +468,10 @@ __global__ void __launch_bounds__(kMaxBlock) group_kernel(const ProjParams p) {
   float2* lut = reinterpret_cast<float2*>(smem4);
   const DevTof& T = p.tof;
   if (MODE != 0 && LUT) {
-    build_lut(lut, T);
+    if (MODE == 1 && T.m > 0)
+      build_lut_aligned(lut, T);
+    else
+      build_lut(lut, T);
     __syncthreads();
   }
   const int N = T.nbins;
@@ -530,7 +591,15 @@ __global__ void __launch_bounds__(kMaxBlock) group_kernel(const ProjParams p) {
             const int t1 = min(N - 1, (int)floorf(x + T.R_over_w));
             const float dlo = (tau - ddl) - ((float)t0 - T.hbin) * T.width;
             float sy = 0.f;
-            if (LUT) {
+            if (LUT && T.m > 0) {
+              const float xl0 = (dlo + T.Rp) * T.inv_hp;
+              const int ix0 = min(max((int)xl0, 0), T.nodes_a - 1);
+              const float fr = xl0 - (float)ix0;
+              for (int t = t0, ix = ix0; t <= t1; ++t, ix -= T.m) {
+                const float2 e = lut[max(ix, 0)];
+                sy = fmaf(fmaf(fr, e.y, e.x), __ldg(yrow + t), sy);
+              }
+            } else if (LUT) {
               const float xl0 = (dlo + T.R) * T.inv_h, step = T.width * T.inv_h;
               for (int t = t0; t <= t1; ++t)
                 sy = fmaf(lut_at(lut, fmaf(-(float)(t - t0), step, xl0), T.nodes - 1), __ldg(yrow + t), sy);
