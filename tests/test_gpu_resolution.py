@@ -133,3 +133,31 @@ def test_slot_graph_with_resolution_model(ops):
         assert rel_l2(x_graph.cpu().numpy(), x_direct.cpu().numpy()) <= 1e-5
         assert rel_l2(x_graph_q.cpu().numpy(), x_direct.cpu().numpy()) <= 1e-5
     srv.close()
+
+
+def test_gauss3d_many_planes_and_large_radius(ops):
+    """More image planes than one grid dimension holds (65535) and radii
+    above the unrolled kernels' 8: the generic pass and the grid loops."""
+    g = synth.ImageGeom((700, 3, 5), (0.0, 0.0, 0.0), (2.0, 2.0, 2.0))
+    rng = np.random.Generator(np.random.PCG64(7340))
+    xs = rng.uniform(0.0, 1.0, size=(100,) + g.shape).astype(np.float32)
+    for fwhm in (4.5, (30.0, 4.5, 4.5)):  # R = 4 on every axis; R = 26 on axis 0 (generic pass)
+        out = ops.jp_gauss3d(torch.from_numpy(xs).cuda(), g, fwhm).cpu().numpy()
+        for i in (0, 57, 99):
+            assert max_err(out[i], oracle.gauss3d(xs[i], g, fwhm)) <= FWD_TOL
+
+
+@pytest.mark.parametrize("path", ["quads", "direct"])
+def test_osem_empty_subsets(ops, path):
+    """A frame with fewer events than subsets: the empty subsets back-project
+    nothing, so the update zeroes the image, as the oracle's does."""
+    from paper_2212_12519_gb300 import osem
+    g, ph, xs, xe, tb, s, b = res_frame()
+    tof = synth.TOF_CLINICAL
+    n = 5
+    x_or = oracle.lm_osem(xs[:n].numpy(), xe[:n].numpy(), tb[:n].numpy(), g, tof, s, b, n_iter=1, n_sub=8)
+    spec = osem.FrameSpec(xs[:n].cuda(), xe[:n].cuda(), tb[:n].cuda(), g, b, n_iter=1, n_sub=8, path=path)
+    x = osem.LMOSEMFrame(spec, torch.from_numpy(s).cuda(), tof).run()
+    torch.cuda.synchronize()
+    assert np.all(np.isfinite(x.cpu().numpy()))
+    assert np.abs(x.cpu().numpy() - x_or).max() <= 1e-6 * max(1.0, np.abs(x_or).max())

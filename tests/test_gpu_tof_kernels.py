@@ -154,3 +154,40 @@ def test_osem_per_event_sigma_vs_oracle(ops, path):
     x = osem.LMOSEMFrame(spec, cuda(s.astype(np.float32)), tof).run()
     torch.cuda.synchronize()
     assert rel_l2(x.cpu().numpy(), x_or) <= 1e-4
+
+
+@pytest.mark.parametrize("table", ["box2", "max_nodes"])
+def test_tabulated_kernel_extremes(ops, table):
+    """The smallest table (2 nodes: a box, value 1 up to the support edge)
+    and the largest (JP_TOF_TABLE nodes), listmode and sinogram."""
+    xs, xe = lors(6_000, seed=7440)
+    n = len(xs)
+    rng = np.random.Generator(np.random.PCG64(7441))
+    img = rng.uniform(0, 3, size=GEOM.shape).astype(np.float32)
+    if table == "box2":
+        tof = synth.TofParams.tabulated(9.0, 13, (1.0, 1.0), 4.5)
+    else:
+        tof = synth.TofParams.tabulated(9.0, 13, skewed_table(2048, 20.0).tolist(), 20.0)
+    tb = rng.integers(-6, 7, size=n).astype(np.int16)
+    for mode in ("tof_lm", "tof_sino"):
+        kw = dict(tof_bin=tb) if mode == "tof_lm" else {}
+        p_or, amb = oracle.fwd(xs, xe, img, GEOM, mode, tof, threads=THREADS, amb_eps=AMB_EPS,
+                               return_amb=True, **kw)
+        plan = ops.jp_plan_create(cuda(xs), cuda(xe), GEOM, tof_bin=cuda(tb), tof_bin_width=tof.bin_width)
+        p = (ops.jp_fwd_tof_lm(plan, cuda(img), tof) if mode == "tof_lm"
+             else ops.jp_fwd_tof_sino(plan, cuda(img), tof))
+        torch.cuda.synchronize()
+        assert fwd_err(p.cpu().numpy(), p_or, amb) <= FWD_TOL, mode
+        plan.destroy()
+
+
+def test_tabulated_kernel_argument_checks(ops):
+    xs, xe = lors(100, seed=7450)
+    plan = ops.jp_plan_create(cuda(xs), cuda(xe), GEOM)
+    img = torch.zeros(GEOM.shape, device="cuda")
+    bad = [synth.TofParams.tabulated(9.0, 13, [1.0] * 4, 0.0),          # half width 0
+           synth.TofParams.tabulated(9.0, 13, [1.0] * 2049, 10.0)]      # more nodes than the table holds
+    for tof in bad:
+        with pytest.raises(ops.JosephError):
+            ops.jp_fwd_tof_sino(plan, img, tof)
+    plan.destroy()
