@@ -3,7 +3,8 @@
 The hot path shards naturally: LORs (or events) split into contiguous ranges
 per rank, every rank holds the image, forward outputs are disjoint, and a
 back projection is a sum over LORs, so the ranks' partial images add up to
-the whole with one sum-allreduce of the image.  Independent frames (the
+the whole with one sum-allreduce of the image; an OSEM subset update needs
+one such allreduce per subset.  Independent frames (the
 benchmark's batches, the served OSEM frames) need no collective at all.
 The local projector is passed in, so the same code runs the CUDA library on
 GPUs and any other projector in tests.
@@ -50,6 +51,19 @@ def fwd_gather(local_fwd: Callable[[int, int], torch.Tensor], n: int, group=None
     out = [torch.empty_like(padded) for _ in sizes]
     dist.all_gather(out, padded, group=group)
     return torch.cat([o[:sz] for o, sz in zip(out, sizes)])
+
+
+def osem_subset_allreduce(x: torch.Tensor, local_bp: Callable[[torch.Tensor], torch.Tensor],
+                          update: Callable[[torch.Tensor, torch.Tensor], torch.Tensor], group=None) -> torch.Tensor:
+    """One OSEM subset update with the subset's events (or LORs) sharded over
+    ranks: every rank back-projects the ratio of its own events,
+    ``local_bp(x)`` (forward projection, ratio and back projection are local
+    per event), one sum-allreduce of the image adds the shards, and every
+    rank applies the same multiplicative ``update(x, bp)``, so the replicas
+    of x stay identical."""
+    bp = local_bp(x)
+    dist.all_reduce(bp, op=dist.ReduceOp.SUM, group=group)
+    return update(x, bp)
 
 
 def max_over_ranks(value: float, device="cpu", group=None) -> float:

@@ -105,3 +105,63 @@ def test_lost_rank_is_detected_not_hung():
         if p.is_alive():
             p.kill()
     assert msg.startswith("error")
+
+
+def _osem_problem():
+    from paper_2212_12519_gb300 import synth
+    g = synth.ImageGeom.centred((14, 12, 8), (2.0, 2.0, 2.0))
+    ph = synth.ellipsoid_phantom(g, synth.PhantomSpec((10.0, 8.0, 5.0), (3.0,)), 81)
+    tof = synth.TOF_CLINICAL
+    xs, xe, tb = synth.lm_events(ph, g, synth.SCANNER_CLINICAL, tof, 2001, seed=82)
+    rng = np.random.Generator(np.random.PCG64(83))
+    sens = rng.uniform(0.5, 2.0, size=g.shape)
+    return g, tof, xs.numpy(), xe.numpy(), tb.numpy(), sens, 0.3
+
+
+def _osem_worker(rank, world, port, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=60))
+    import oracle
+    from paper_2212_12519_gb300 import dist as jdist
+    g, tof, xs, xe, tb, sens, b = _osem_problem()
+    n_sub = 4
+    x = torch.from_numpy((sens > 0).astype(np.float64))
+    for m in range(n_sub):
+        sx, se, st = xs[m::n_sub], xe[m::n_sub], tb[m::n_sub]
+        s, e = jdist.shard(len(sx), rank, world)
+
+        def local_bp(xc, s=s, e=e, sx=sx, se=se, st=st):
+            p = oracle.fwd(sx[s:e], se[s:e], xc.numpy(), g, "tof_lm", tof, tof_bin=st[s:e])
+            return torch.from_numpy(oracle.back(sx[s:e], se[s:e], 1.0 / (p + b), g, "tof_lm", tof, tof_bin=st[s:e]))
+
+        def update(xc, bp):
+            sc = torch.from_numpy(sens / n_sub)
+            return torch.where(sc > 0, xc * bp / torch.where(sc > 0, sc, torch.ones_like(sc)), torch.zeros_like(xc))
+
+        x = jdist.osem_subset_allreduce(x, local_bp, update)
+    q.put((rank, x.numpy()))
+    dist.destroy_process_group()
+
+
+def test_two_rank_osem_subsets_equal_single_process():
+    """LM-OSEM with each subset's events split over two ranks and one image
+    allreduce per subset: both replicas equal the single-process oracle
+    OSEM."""
+    import oracle
+    oracle.build()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_osem_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = dict(q.get(timeout=120) for _ in range(2))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    g, tof, xs, xe, tb, sens, b = _osem_problem()
+    whole = oracle.lm_osem(xs, xe, tb, g, tof, sens, b, n_iter=1, n_sub=4)
+    for r in (0, 1):
+        assert np.abs(got[r] - whole).max() <= 1e-11 * np.abs(whole).max()
+    assert np.array_equal(got[0], got[1])
