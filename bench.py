@@ -122,25 +122,32 @@ def measured_peaks():
 # workload
 # ---------------------------------------------------------------------------
 def make_tof_lm_batch(rank: int, n_frames: int, events: int, device):
-    """8 phantoms x ``events`` TOF listmode events each (seeded per frame and rank)."""
+    """8 phantoms x ``events`` TOF listmode events each (seeded per frame and
+    rank), as recorded listmode data: two detector indices and a TOF bin per
+    event, plus the scanner's detector table (the LOR endpoints are kept
+    too, for the oracle sample and the autotuner)."""
     from paper_2212_12519_gb300 import synth
     g = synth.GEOM_CLINICAL
     tof = synth.TOF_CLINICAL
-    imgs, xs_l, xe_l, tb_l, bvals = [], [], [], [], []
+    imgs, xs_l, xe_l, tb_l, ds_l, de_l, bvals = [], [], [], [], [], [], []
     for f in range(n_frames):
         seed = 4001 + f + 1000 * 100 * rank
         ph = synth.ellipsoid_phantom(g, synth.PHANTOM_CLINICAL, seed, device=device)
-        xs, xe, tb = synth.lm_events(ph, g, synth.SCANNER_CLINICAL, tof, events, seed=seed + 50,
-                                     device=device)
+        xs, xe, tb, ds, de = synth.lm_events(ph, g, synth.SCANNER_CLINICAL, tof, events, seed=seed + 50,
+                                             device=device, return_det=True)
         imgs.append(ph)
         xs_l.append(xs)
         xe_l.append(xe)
         tb_l.append(tb)
+        ds_l.append(ds)
+        de_l.append(de)
         bvals.append(synth.background_level(ph, tof))
     xs = torch.cat(xs_l)
     xe = torch.cat(xe_l)
     tb = torch.cat(tb_l)
-    del xs_l, xe_l, tb_l
+    ds = torch.cat(ds_l)
+    de = torch.cat(de_l)
+    del xs_l, xe_l, tb_l, ds_l, de_l
     w = synth.loss_weights(xs.shape[0], 4999 + rank, device=device)
     offsets = [events * f for f in range(n_frames + 1)]
     bvec = torch.repeat_interleave(torch.tensor(bvals, dtype=torch.float32, device=device),
@@ -148,6 +155,7 @@ def make_tof_lm_batch(rank: int, n_frames: int, events: int, device):
     x = torch.stack(imgs).contiguous()
     bframe = torch.tensor(bvals, dtype=torch.float32, device=device)
     return dict(geom=g, tof=tof, xs=xs.contiguous(), xe=xe.contiguous(), tb=tb.contiguous(),
+                ds=ds.contiguous(), de=de.contiguous(), det=synth.SCANNER_CLINICAL.crystal_table(device),
                 w=w, bvec=bvec.contiguous(), bframe=bframe, x=x, offsets=offsets, bvals=bvals)
 
 
@@ -182,8 +190,8 @@ def run_ours(args):
             opts = autotune.tune(W["xs"][:epf], W["xe"][:epf], g, mode="nontof")
         else:
             opts = autotune.tune(W["xs"][:epf], W["xe"][:epf], g, mode="tof_lm", tof=tof, tof_bin=W["tb"][:epf])
-    plan = ops.jp_plan_create_batch(W["xs"], W["xe"], g, W["offsets"], tof_bin=W["tb"],
-                                    tof_bin_width=0.0 if nontof else tof.bin_width, **opts)
+    plan = ops.jp_plan_create_batch_det(W["ds"], W["de"], W["det"], g, W["offsets"], tof_bin=W["tb"],
+                                        tof_bin_width=0.0 if nontof else tof.bin_width, **opts)
     if nontof:
         # background: 10 % of each frame's mean non-TOF projection
         p0 = ops.jp_fwd(plan, W["x"]).view(n_frames, epf).double().mean(dim=1)
@@ -223,9 +231,10 @@ def run_ours(args):
 
     def step(record=True):
         if record:
-            timed("bin", lambda: ops.jp_plan_rebind(plan, W["xs"], W["xe"], W["offsets"], tof_bin=W["tb"]))
+            timed("bin", lambda: ops.jp_plan_rebind_det(plan, W["ds"], W["de"], W["det"], W["offsets"],
+                                                        tof_bin=W["tb"]))
         else:
-            ops.jp_plan_rebind(plan, W["xs"], W["xe"], W["offsets"], tof_bin=W["tb"])
+            ops.jp_plan_rebind_det(plan, W["ds"], W["de"], W["det"], W["offsets"], tof_bin=W["tb"])
         x.grad = None
         if record:
             p = TimedTOFLM.apply(x)
@@ -280,7 +289,7 @@ def run_ours(args):
     if rank == 0 and not args.no_cpu_baseline:
         cpu_sample = _oracle_events(W, min(W["xs"].shape[0], 8_000_000))
     plan.destroy()
-    del W["xs"], W["xe"], W["w"], W["bvec"]
+    del W["xs"], W["xe"], W["ds"], W["de"], W["w"], W["bvec"]
     W["tb"] = None
     torch.cuda.empty_cache()
     serving = None
@@ -308,6 +317,8 @@ def run_ours(args):
             "config": {"workload": f"{'nontof' if nontof else 'tof'}_lm_batch{n_frames}x{epf // 1_000_000}M_200x200x71",
                        "frames_per_gpu": n_frames, "events_per_frame": epf, "image": list(g.shape),
                        "tof_bins": 0 if nontof else tof.n_bins,
+                       "input": "listmode as recorded: int32 detector-index pairs"
+                                + ("" if nontof else " + int16 TOF bin") + " per event, float32 detector table",
                        "l2": "inputs (>10 GB/step) larger than L2, no flush",
                        "parallelism": f"dp{ws} (independent batches)", "plan_opts": opts},
             "kernel_ms": kern,
@@ -346,7 +357,7 @@ def run_e2e(args, W, plan, g, tof, dev, ws, nontof=False):
     copies overlap the compute; the timed region holds all of them."""
     from paper_2212_12519_gb300 import ops
     from paper_2212_12519_gb300.autograd import JosephNonTOF, JosephTOFLM, PoissonLogLik
-    keys = ("xs", "xe", "w", "bframe", "x") if nontof else ("xs", "xe", "tb", "w", "bframe", "x")
+    keys = ("ds", "de", "det", "w", "bframe", "x") if nontof else ("ds", "de", "det", "tb", "w", "bframe", "x")
     host = {k: W[k].cpu().pin_memory() for k in keys}
     dbuf = [{k: torch.empty_like(W[k]) for k in keys} for _ in range(2)]
     out_grad = [torch.empty(W["x"].shape, dtype=torch.float32).pin_memory() for _ in range(2)]
@@ -369,7 +380,7 @@ def run_e2e(args, W, plan, g, tof, dev, ws, nontof=False):
     def compute(b):
         comp.wait_event(copied[b])
         d = dbuf[b]
-        ops.jp_plan_rebind(plan, d["xs"], d["xe"], W["offsets"], tof_bin=d.get("tb"))
+        ops.jp_plan_rebind_det(plan, d["ds"], d["de"], d["det"], W["offsets"], tof_bin=d.get("tb"))
         x = d["x"].detach().requires_grad_(True)
         p = JosephNonTOF.apply(x, plan) if nontof else JosephTOFLM.apply(x, plan, tof)
         loss = PoissonLogLik.apply(p, plan, d["w"], d["bframe"])

@@ -172,6 +172,27 @@ int jp_plan_rebind(jp_plan p, const float* xstart, const float* xend, const int1
                    int32_t n_frames, void* stream);
 
 /*
+ * Detector-index input (listmode data as recorded: a pair of detector
+ * indices per event).  det_start / det_end are device int32 [n_total]
+ * indices into det_xyz, a device float32 [n_det][3] table of detector
+ * coordinates (mm); LOR j runs from det_xyz[det_start[j]] to
+ * det_xyz[det_end[j]].  The endpoints are read through the table while the
+ * LORs are binned, so the plan is the one jp_plan_create_batch /
+ * jp_plan_rebind would build from the gathered coordinates, bit for bit.
+ * An index outside [0, n_det) gives the empty LOR (xs = xe = 0: no samples).
+ * Other arguments and errors as jp_plan_create_batch / jp_plan_rebind; also
+ * JP_ERR_ARG for n_det < 1 or NULL detector arrays with n_total > 0.
+ */
+int jp_plan_create_batch_det(jp_plan* out, const int32_t* det_start, const int32_t* det_end,
+                             const float* det_xyz, int32_t n_det, const int16_t* tof_bin,
+                             const float* tof_center_offset, const int64_t* frame_offsets,
+                             int32_t n_frames, const jp_image_geom* g, const jp_plan_opts* opts,
+                             void* stream);
+int jp_plan_rebind_det(jp_plan p, const int32_t* det_start, const int32_t* det_end, const float* det_xyz,
+                       int32_t n_det, const int16_t* tof_bin, const float* tof_center_offset,
+                       const int64_t* frame_offsets, int32_t n_frames, void* stream);
+
+/*
  * jp_plan_set_event_sigma -- per-event TOF resolution for a TOF-listmode
  * plan: sigma is a device float32 array of the bound LORs' Gaussian sigmas
  * (mm) in caller order (n_total entries); it is gathered into the plan's

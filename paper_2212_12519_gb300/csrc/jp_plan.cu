@@ -39,6 +39,11 @@ __device__ __forceinline__ int frame_of(const int64_t* __restrict__ off, int n_f
 struct KeyParams {
   const float* xs;
   const float* xe;
+  // detector-index input (xs / xe NULL): endpoints are det_xyz[ds[j]], det_xyz[de[j]]
+  const int32_t* ds;
+  const int32_t* de;
+  const float* dxyz;
+  int32_t n_det;
   const int16_t* tof_bin;
   const float* delta;
   int64_t n;
@@ -53,14 +58,34 @@ struct KeyParams {
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
+// endpoints of caller LOR j, from the coordinate arrays or from the detector
+// table; an index outside [0, n_det) gives the empty LOR xs = xe = 0
+__device__ __forceinline__ void lor_endpoints(const KeyParams& p, int64_t j, float xs[3], float xe[3]) {
+  if (p.dxyz) {
+    const int32_t a = __ldg(p.ds + j), b = __ldg(p.de + j);
+    const bool ok = (unsigned)a < (unsigned)p.n_det && (unsigned)b < (unsigned)p.n_det;
+    const float* pa = p.dxyz + 3 * (int64_t)(ok ? a : 0);
+    const float* pb = p.dxyz + 3 * (int64_t)(ok ? b : 0);
+    for (int i = 0; i < 3; ++i) {
+      xs[i] = ok ? __ldg(pa + i) : 0.f;
+      xe[i] = ok ? __ldg(pb + i) : 0.f;
+    }
+  } else {
+    for (int i = 0; i < 3; ++i) {
+      xs[i] = p.xs[3 * j + i];
+      xe[i] = p.xe[3 * j + i];
+    }
+  }
+}
+
 __global__ void key_kernel(KeyParams p, uint32_t* __restrict__ keys, uint32_t* __restrict__ hist) {
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= p.n) return;
   int f = p.interleaved ? (int)(j % p.n_frames) : frame_of(p.frame_off, p.n_frames, j);
   uint32_t key = 0;
   if (!p.keep_order) {
-    float xs[3] = {p.xs[3 * j], p.xs[3 * j + 1], p.xs[3 * j + 2]};
-    float xe[3] = {p.xe[3 * j], p.xe[3 * j + 1], p.xe[3 * j + 2]};
+    float xs[3], xe[3];
+    lor_endpoints(p, j, xs, xe);
     const float d0 = xe[0] - xs[0], d1 = xe[1] - xs[1], d2 = xe[2] - xs[2];
     const int a = principal_axis(xs, xe);
     const int b = (a == 0) ? 1 : 0;
@@ -213,8 +238,10 @@ __global__ void scatter_kernel(KeyParams p, const uint32_t* __restrict__ keys, u
     // LOR costs one scattered 32-byte sector instead of two
     const float w0 = p.delta ? p.delta[j] : __int_as_float((int)j);
     const int tb = p.tof_bin ? (int)p.tof_bin[j] : 0;
-    lor[2 * (int64_t)pos[q]] = make_float4(p.xs[3 * j], p.xs[3 * j + 1], p.xs[3 * j + 2], w0);
-    lor[2 * (int64_t)pos[q] + 1] = make_float4(p.xe[3 * j], p.xe[3 * j + 1], p.xe[3 * j + 2], __int_as_float(tb));
+    float xs[3], xe[3];
+    lor_endpoints(p, j, xs, xe);
+    lor[2 * (int64_t)pos[q]] = make_float4(xs[0], xs[1], xs[2], w0);
+    lor[2 * (int64_t)pos[q] + 1] = make_float4(xe[0], xe[1], xe[2], __int_as_float(tb));
     if (p.delta) perm[pos[q]] = (int32_t)j;
   }
 }
@@ -255,8 +282,17 @@ int validate_offsets(const int64_t* off, int32_t n_frames, int64_t* n_total) {
   return JP_OK;
 }
 
+// The LORs come either as coordinate arrays (xs, xe) or as detector
+// indices into a detector coordinate table (det != nullptr).
+struct DetInput {
+  const int32_t* ds;
+  const int32_t* de;
+  const float* xyz;
+  int32_t n_det;
+};
+
 int bind(jp_plan p, const float* xs, const float* xe, const int16_t* tof_bin, const float* delta,
-         const int64_t* off, int32_t n_frames, cudaStream_t st) {
+         const int64_t* off, int32_t n_frames, cudaStream_t st, const DetInput* det = nullptr) {
   int64_t n = 0;
   const bool interleaved = (p->opts.flags & JP_PLAN_INTERLEAVED) != 0;
   if (interleaved) {
@@ -270,7 +306,14 @@ int bind(jp_plan p, const float* xs, const float* xe, const int16_t* tof_bin, co
   int rc = JP_OK;
   if (n > p->capacity || n_frames > p->frame_capacity)
     return fail(JP_ERR_ARG, "rebind exceeds the plan's capacity");
-  if (n > 0 && (!xs || !xe)) return fail(JP_ERR_ARG, "xstart/xend is NULL");
+  if (det) {
+    if (n > 0 && (!det->ds || !det->de || !det->xyz)) return fail(JP_ERR_ARG, "det_start/det_end/det_xyz is NULL");
+    if (det->n_det < 1) return fail(JP_ERR_ARG, "n_det must be >= 1");
+    if (!aligned(det->ds, 4) || !aligned(det->de, 4) || !aligned(det->xyz, 4))
+      return fail(JP_ERR_ALIGN, "misaligned detector arrays");
+  } else if (n > 0 && (!xs || !xe)) {
+    return fail(JP_ERR_ARG, "xstart/xend is NULL");
+  }
   // a new binding invalidates the per-event sigma gathered for the old one
   p->has_sigma = false;
   if (!aligned(xs, 4) || !aligned(xe, 4) || !aligned(tof_bin, 2) || !aligned(delta, 4))
@@ -303,7 +346,10 @@ int bind(jp_plan p, const float* xs, const float* xe, const int16_t* tof_bin, co
     return JP_OK;
   }
   KeyParams kp;
-  kp.xs = xs; kp.xe = xe; kp.tof_bin = tof_bin; kp.delta = delta; kp.n = n;
+  kp.xs = det ? nullptr : xs; kp.xe = det ? nullptr : xe;
+  kp.ds = det ? det->ds : nullptr; kp.de = det ? det->de : nullptr;
+  kp.dxyz = det ? det->xyz : nullptr; kp.n_det = det ? det->n_det : 0;
+  kp.tof_bin = tof_bin; kp.delta = delta; kp.n = n;
   kp.frame_off = p->frame_off_dev; kp.n_frames = n_frames; kp.g = g;
   kp.slope_bins = p->dims.slope_bins; kp.offset_bins = p->dims.offset_bins;
   kp.window_bins = p->dims.window_bins; kp.zoff_bins = p->dims.zoff_bins;
@@ -364,10 +410,9 @@ void free_plan(jp_plan p) {
 
 using namespace jp;
 
-extern "C" int jp_plan_create_batch(jp_plan* out, const float* xs, const float* xe,
-                                    const int16_t* tof_bin, const float* delta,
-                                    const int64_t* off, int32_t n_frames, const jp_image_geom* g,
-                                    const jp_plan_opts* opts, void* stream) {
+static int create_batch(jp_plan* out, const float* xs, const float* xe, const int16_t* tof_bin, const float* delta,
+                        const int64_t* off, int32_t n_frames, const jp_image_geom* g, const jp_plan_opts* opts,
+                        void* stream, const DetInput* det) {
   clear_error();
   if (!out) return fail(JP_ERR_ARG, "out is NULL");
   *out = nullptr;
@@ -450,13 +495,28 @@ extern "C" int jp_plan_create_batch(jp_plan* out, const float* xs, const float* 
     return fail(e == cudaErrorMemoryAllocation ? JP_ERR_NOMEM : JP_ERR_CUDA,
                 std::string("plan allocation: ") + cudaGetErrorString(e));
   }
-  rc = bind(p, xs, xe, tof_bin, delta, off, n_frames, (cudaStream_t)stream);
+  rc = bind(p, xs, xe, tof_bin, delta, off, n_frames, (cudaStream_t)stream, det);
   if (rc) {
     free_plan(p);
     return rc;
   }
   *out = p;
   return JP_OK;
+}
+
+extern "C" int jp_plan_create_batch(jp_plan* out, const float* xs, const float* xe,
+                                    const int16_t* tof_bin, const float* delta,
+                                    const int64_t* off, int32_t n_frames, const jp_image_geom* g,
+                                    const jp_plan_opts* opts, void* stream) {
+  return create_batch(out, xs, xe, tof_bin, delta, off, n_frames, g, opts, stream, nullptr);
+}
+
+extern "C" int jp_plan_create_batch_det(jp_plan* out, const int32_t* det_start, const int32_t* det_end,
+                                        const float* det_xyz, int32_t n_det, const int16_t* tof_bin,
+                                        const float* delta, const int64_t* off, int32_t n_frames,
+                                        const jp_image_geom* g, const jp_plan_opts* opts, void* stream) {
+  const DetInput det{det_start, det_end, det_xyz, n_det};
+  return create_batch(out, nullptr, nullptr, tof_bin, delta, off, n_frames, g, opts, stream, &det);
 }
 
 extern "C" int jp_plan_create(jp_plan* out, const float* xs, const float* xe,
@@ -518,6 +578,15 @@ extern "C" int jp_plan_rebind(jp_plan p, const float* xs, const float* xe, const
   clear_error();
   if (!p) return fail(JP_ERR_ARG, "plan is NULL");
   return bind(p, xs, xe, tof_bin, delta, off, n_frames, (cudaStream_t)stream);
+}
+
+extern "C" int jp_plan_rebind_det(jp_plan p, const int32_t* det_start, const int32_t* det_end, const float* det_xyz,
+                                  int32_t n_det, const int16_t* tof_bin, const float* delta, const int64_t* off,
+                                  int32_t n_frames, void* stream) {
+  clear_error();
+  if (!p) return fail(JP_ERR_ARG, "plan is NULL");
+  const DetInput det{det_start, det_end, det_xyz, n_det};
+  return bind(p, nullptr, nullptr, tof_bin, delta, off, n_frames, (cudaStream_t)stream, &det);
 }
 
 extern "C" int jp_plan_destroy(jp_plan p) {

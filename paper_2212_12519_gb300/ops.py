@@ -64,6 +64,8 @@ _SIGS = {
     "jp_plan_rebind": [P, P, P, P, P, P, I32, P],
     "jp_plan_destroy": [P],
     "jp_plan_set_event_sigma": [P, P, P],
+    "jp_plan_create_batch_det": [ctypes.POINTER(P), P, P, P, I32, P, P, P, I32, P, P, P],
+    "jp_plan_rebind_det": [P, P, P, P, I32, P, P, P, I32, P],
     "jp_plan_info": [P, P, P, P, P],
     "jp_fwd": [P, P, I64, P, P],
     "jp_back": [P, P, P, I64, P],
@@ -263,6 +265,50 @@ def jp_plan_create_subsets(xs, xe, geom, n_subsets, tof_bin=None, delta=None, st
     plan = jp_plan_create_batch(xs, xe, geom, off, tof_bin, delta, stream, interleaved=True, **opts)
     plan.frame_offsets = [sum(n // n_subsets + (1 if f < n % n_subsets else 0) for f in range(m))
                           for m in range(n_subsets + 1)]
+    return plan
+
+
+def _det(det_start, det_end, det_xyz):
+    if det_start.dim() != 1 or det_start.shape != det_end.shape:
+        raise ValueError("det_start/det_end must be 1-D of equal length")
+    if det_xyz.dim() != 2 or det_xyz.shape[1] != 3:
+        raise ValueError("det_xyz must be [n_det, 3]")
+    return (_ptr(det_start, torch.int32, "det_start"), _ptr(det_end, torch.int32, "det_end"),
+            _ptr(det_xyz, torch.float32, "det_xyz"), int(det_xyz.shape[0]))
+
+
+def jp_plan_create_batch_det(det_start, det_end, det_xyz, geom, frame_offsets, tof_bin=None, delta=None,
+                             stream=None, **opts) -> Plan:
+    """Plan from detector-index listmode events: LOR j runs from
+    det_xyz[det_start[j]] to det_xyz[det_end[j]] (int32 indices, float32
+    [n_det, 3] table, all on the device)."""
+    pds, pde, pxyz, nd = _det(det_start, det_end, det_xyz)
+    off = (ctypes.c_int64 * len(frame_offsets))(*[int(v) for v in frame_offsets])
+    h = P()
+    g = image_geom(geom)
+    o = _opts(**opts)
+    _check(load().jp_plan_create_batch_det(ctypes.byref(h), pds, pde, pxyz, nd,
+                                           _ptr(tof_bin, torch.int16, "tof_bin"),
+                                           _ptr(delta, torch.float32, "delta"), off, len(frame_offsets) - 1,
+                                           ctypes.byref(g), ctypes.byref(o), _stream(stream)))
+    return Plan(h.value, geom, int(frame_offsets[-1]), len(frame_offsets) - 1, frame_offsets,
+                tof_bin is not None)
+
+
+def jp_plan_rebind_det(plan: Plan, det_start, det_end, det_xyz, frame_offsets=None, tof_bin=None, delta=None,
+                       stream=None):
+    """Rebinds a plan to detector-index events (no allocation)."""
+    pds, pde, pxyz, nd = _det(det_start, det_end, det_xyz)
+    if frame_offsets is None:
+        frame_offsets = [0, int(det_start.shape[0])]
+    off = (ctypes.c_int64 * len(frame_offsets))(*[int(v) for v in frame_offsets])
+    _check(load().jp_plan_rebind_det(plan.handle, pds, pde, pxyz, nd, _ptr(tof_bin, torch.int16, "tof_bin"),
+                                     _ptr(delta, torch.float32, "delta"), off, len(frame_offsets) - 1,
+                                     _stream(stream)))
+    plan.n = int(frame_offsets[-1])
+    plan.n_frames = len(frame_offsets) - 1
+    plan.frame_offsets = list(frame_offsets)
+    plan.has_tof_bin = tof_bin is not None
     return plan
 
 

@@ -112,6 +112,11 @@ class Scanner:
     def half_axial(self) -> float:
         return (self.n_rings / 2.0) * self.ring_spacing
 
+    def crystal_table(self, device="cpu") -> torch.Tensor:
+        """float32 [n_rings * n_crystals, 3] detector coordinates; detector
+        index r * n_crystals + c (the listmode events' index form)."""
+        return self.crystal_xyz(device).reshape(-1, 3).to(torch.float32).contiguous()
+
 
 # --------------------------------------------------------------------------
 # workload definitions
@@ -268,7 +273,7 @@ def background_level(phantom: torch.Tensor, tof: TofParams, fraction: float = 0.
 # listmode events (Monte-Carlo emission + detection)
 # --------------------------------------------------------------------------
 def lm_events(phantom: torch.Tensor, geom: ImageGeom, scanner: Scanner, tof: TofParams,
-              n_events: int, seed: int, device="cpu", chunk: int = 1 << 22):
+              n_events: int, seed: int, device="cpu", chunk: int = 1 << 22, return_det: bool = False):
     """TOF listmode events drawn by simulating emissions in the phantom.
 
     1. emission point: voxel drawn with probability proportional to its value,
@@ -282,7 +287,9 @@ def lm_events(phantom: torch.Tensor, geom: ImageGeom, scanner: Scanner, tof: Tof
        t = round(tau_meas / bin_width), events with |t| > (n_bins-1)/2 dropped;
     4. the endpoints are swapped with probability 1/2 (negating t).
 
-    Returns float32 xs, xe [n, 3] and int16 signed TOF bins [n] on ``device``.
+    Returns float32 xs, xe [n, 3] and int16 signed TOF bins [n] on ``device``;
+    with ``return_det`` also the int32 detector indices [n] of the two
+    endpoints (r * n_crystals + c, so xs == scanner.crystal_table()[ds]).
     """
     gen = torch.Generator(device=device)
     gen.manual_seed(int(seed))
@@ -308,7 +315,7 @@ def lm_events(phantom: torch.Tensor, geom: ImageGeom, scanner: Scanner, tof: Tof
     cmax = min(1.0, 1.05 * slope / math.sqrt(1.0 + slope * slope))
     hmax = (tof.n_bins - 1) // 2
 
-    outs_s, outs_e, outs_t = [], [], []
+    outs_s, outs_e, outs_t, outs_ds, outs_de = [], [], [], [], []
     got = 0
     while got < n_events:
         m = chunk
@@ -359,15 +366,21 @@ def lm_events(phantom: torch.Tensor, geom: ImageGeom, scanner: Scanner, tof: Tof
         xs2 = torch.where(swap[:, None], xe, xs)
         xe2 = torch.where(swap[:, None], xs, xe)
         t2 = torch.where(swap, -t, t)
+        d1, d2 = r1c * nc + c1, r2c * nc + c2
         sel = torch.nonzero(ok).squeeze(1)
         take = min(int(sel.numel()), n_events - got)
         sel = sel[:take]
         outs_s.append(xs2[sel].float())
         outs_e.append(xe2[sel].float())
         outs_t.append(t2[sel].to(torch.int16))
+        if return_det:
+            outs_ds.append(torch.where(swap, d2, d1)[sel].to(torch.int32))
+            outs_de.append(torch.where(swap, d1, d2)[sel].to(torch.int32))
         got += take
-    return (torch.cat(outs_s).contiguous(), torch.cat(outs_e).contiguous(),
-            torch.cat(outs_t).contiguous())
+    out = (torch.cat(outs_s).contiguous(), torch.cat(outs_e).contiguous(), torch.cat(outs_t).contiguous())
+    if return_det:
+        out = out + (torch.cat(outs_ds).contiguous(), torch.cat(outs_de).contiguous())
+    return out
 
 
 def loss_weights(n: int, seed: int, device="cpu") -> torch.Tensor:

@@ -341,3 +341,47 @@ def test_degenerate_axes(ops, shape):
         torch.cuda.synchronize()
         if np.abs(b_or).max() > 0:
             assert rel_l2(out.cpu().numpy(), b_or) <= BACK_TOL, mode
+
+
+def test_detector_index_plans(ops, clinical_img):
+    """Plans from detector-index events equal plans from the gathered
+    coordinates: identical forward projections, back projections equal up
+    to summation order, and against the oracle; an index outside the
+    table gives an empty LOR; rebinding to other events works."""
+    g = synth.GEOM_CLINICAL
+    tof = synth.TOF_CLINICAL
+    sc = synth.SCANNER_CLINICAL
+    xs, xe, tb, ds, de = synth.lm_events(torch.from_numpy(clinical_img), g, sc, tof, 120_001, seed=4601,
+                                         return_det=True)
+    table = sc.crystal_table("cuda")
+    img = cuda(clinical_img)
+    ds_c, de_c = ds.cuda(), de.cuda()
+    ds_c[::5000] = -1
+    de_c[7::5000] = table.shape[0]
+    bad = (ds_c < 0) | (de_c >= table.shape[0])
+    cuts = [0, 50_000, 120_001]
+    pd = ops.jp_plan_create_batch_det(ds_c, de_c, table, g, cuts, tof_bin=tb.cuda(), tof_bin_width=tof.bin_width)
+    pc = ops.jp_plan_create_batch(xs.cuda(), xe.cuda(), g, cuts, tof_bin=tb.cuda(), tof_bin_width=tof.bin_width)
+    imgs = torch.stack([img, 0.5 * img]).contiguous()
+    fd = ops.jp_fwd_tof_lm(pd, imgs, tof)
+    fc = ops.jp_fwd_tof_lm(pc, imgs, tof)
+    assert torch.equal(fd[~bad], fc[~bad])
+    assert float(fd[bad].abs().max()) == 0.0
+    y = torch.rand(cuts[-1], device="cuda")
+    y[bad] = 0.0
+    bd = ops.jp_back_tof_lm(pd, y, tof, torch.zeros_like(imgs))
+    bc = ops.jp_back_tof_lm(pc, y, tof, torch.zeros_like(imgs))
+    assert rel_l2(bd.cpu().numpy(), bc.cpu().numpy().astype(np.float64)) <= 1e-6
+    ok = (~bad).cpu().numpy()
+    p_or, amb = oracle.fwd(xs.numpy()[:50_000][ok[:50_000]], xe.numpy()[:50_000][ok[:50_000]], clinical_img, g,
+                           "tof_lm", tof, tof_bin=tb.numpy()[:50_000][ok[:50_000]], threads=THREADS,
+                           amb_eps=AMB_EPS, return_amb=True)
+    assert fwd_err(fd[:50_000][~bad[:50_000]].cpu().numpy(), p_or, amb) <= FWD_TOL
+    # rebind to the second half of the events as one frame
+    ops.jp_plan_rebind_det(pd, ds.cuda()[60_000:], de.cuda()[60_000:], table, tof_bin=tb.cuda()[60_000:])
+    f2 = ops.jp_fwd_tof_lm(pd, img, tof).cpu().numpy()
+    p_or2, amb2 = oracle.fwd(xs.numpy()[60_000:], xe.numpy()[60_000:], clinical_img, g, "tof_lm", tof,
+                             tof_bin=tb.numpy()[60_000:], threads=THREADS, amb_eps=AMB_EPS, return_amb=True)
+    assert fwd_err(f2, p_or2, amb2) <= FWD_TOL
+    pd.destroy()
+    pc.destroy()
