@@ -120,3 +120,17 @@ def test_binding_constants_match_header():
     assert int(defs["JP_OSEM_DIRECT_VOXELS_PER_EVENT"]) == ops.OSEM_DIRECT_VOXELS_PER_EVENT
     assert {k: int(defs["JP_OSEM_PATH_" + k.upper()]) for k in ops.OSEM_PATHS} == ops.OSEM_PATHS
     assert int(defs["JP_PLAN_INTERLEAVED"]) == ops.JP_PLAN_INTERLEAVED
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without the compiled library every entry point raises: there is no
+    CPU or PyTorch fallback behind the binding."""
+    import torch
+    from paper_2212_12519_gb300 import ops, synth
+    monkeypatch.setattr(ops, "_lib", None)
+    monkeypatch.setattr(ops, "lib_path", lambda: str(tmp_path / "absent" / "libjoseph.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        ops.load()
+    g = synth.GEOM_SMALL
+    with pytest.raises(RuntimeError, match="not built"):
+        ops.jp_gauss3d(torch.zeros(g.shape), g, 4.5)
