@@ -631,6 +631,17 @@ __global__ void __launch_bounds__(kMaxBlock) group_kernel(const ProjParams p) {
 // p.quads), ratio 1 / (p + b), back projection of the ratio into p.quads_bp.
 // G lanes per event as in group_kernel; both quad sets are plane-fastest.
 // ---------------------------------------------------------------------------
+// a[0] += v0, a[1] += v1: one 8-byte vector reduction when a is 8-byte
+// aligned, else two scalar ones
+__device__ __forceinline__ void red_pair(float* a, float v0, float v1) {
+  if ((reinterpret_cast<uintptr_t>(a) & 7u) == 0) {
+    atomicAdd(reinterpret_cast<float2*>(a), make_float2(v0, v1));
+  } else {
+    atomicAdd(a, v0);
+    atomicAdd(a + 1, v1);
+  }
+}
+
 // DIRECT = false: forward from the plane-fastest quads of p.img_in (p.quads),
 // back projection into the back-projection quads (p.quads_bp), one 16-byte
 // load / reduction per sample.  DIRECT = true: forward from the image
@@ -759,10 +770,17 @@ __global__ void __launch_bounds__(kMaxBlock) osem_kernel(const ProjParams p) {
           const bool i0 = (unsigned)i < (unsigned)nb, i1 = (unsigned)(i + 1) < (unsigned)nb;
           const bool j0 = (unsigned)j < (unsigned)nc, j1 = (unsigned)(j + 1) < (unsigned)nc;
           const int64_t idx = (int64_t)k * sa + (int64_t)i * sb + (int64_t)j * sc;
-          if (i0 && j0) atomicAdd(p.img_out + idx, ca * (1.f - be));
-          if (i1 && j0) atomicAdd(p.img_out + idx + sb, cb * (1.f - be));
-          if (i0 && j1) atomicAdd(p.img_out + idx + sc, ca * be);
-          if (i1 && j1) atomicAdd(p.img_out + idx + sb + sc, cb * be);
+          if (sc == 1 && j0 && j1) {
+            // (j, j+1) are adjacent floats: an 8-byte-aligned pair takes one
+            // vector reduction instead of two
+            if (i0) red_pair(p.img_out + idx, ca * (1.f - be), ca * be);
+            if (i1) red_pair(p.img_out + idx + sb, cb * (1.f - be), cb * be);
+          } else {
+            if (i0 && j0) atomicAdd(p.img_out + idx, ca * (1.f - be));
+            if (i1 && j0) atomicAdd(p.img_out + idx + sb, cb * (1.f - be));
+            if (i0 && j1) atomicAdd(p.img_out + idx + sc, ca * be);
+            if (i1 && j1) atomicAdd(p.img_out + idx + sb + sc, cb * be);
+          }
         } else {
           atomicAdd(p.quads_bp + qoff + (((int)fu + 1) * nc2 + ((int)fw + 1)) * nap + k,
                     make_float4(ca * (1.f - be), cb * (1.f - be), ca * be, cb * be));
