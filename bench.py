@@ -600,7 +600,7 @@ def run_sino_osem(args):
 
 
 def run_lm_osem_iter(args):
-    """Paper Sec. 3/5's LM-OSEM timing: one TOF listmode OSEM iteration
+    """The paper's LM-OSEM timing (Sec. 3, discussed in Sec. 4): one TOF listmode OSEM iteration
     (34 subset updates, each with the two resolution-model convolutions)
     for one frame of 40e6 and of 1.25e6 events on the 200x200x71 grid.
     The frame's subset plan (binning) is built once before its iterations
@@ -648,7 +648,7 @@ def run_lm_osem_iter(args):
 
 
 def run_layout_study(args):
-    """Paper Sec. 3's memory-layout benchmark: forward + back projection of one
+    """The paper's memory-layout benchmark (Sec. 2.6 and 3): forward + back projection of one
     34-subset sinogram (one view subset of the clinical span-1 sinogram,
     ~4M LORs, paper: 415 x 8 x 1292) for every sinogram order (PVR, VRP,
     RVP) x image symmetry axis (0, 1, 2), non-TOF and TOF, through the

@@ -75,7 +75,7 @@ typedef struct {
 /* TOF kernel: bin width (mm), Gaussian sigma (mm, = FWHM / 2.35482),
  * truncation in sigmas, number of sinogram TOF bins (unused in listmode).
  *
- * Optional tabulated kernel (paper Sec. 5: a 1D lookup table allows
+ * Optional tabulated kernel (paper Sec. 4: a 1D lookup table allows
  * non-Gaussian TOF kernels): when `kernel` is non-NULL it is a device array
  * of `kernel_nodes` float32 values (2 .. JP_TOF_TABLE) of the bin response
  * at the signed distances d_e = -h + e * 2h / (kernel_nodes - 1) from the bin
@@ -267,7 +267,7 @@ int jp_osem_update(float* x, const float* bp, const float* sens, float scale, in
 
 /*
  * jp_osem_ratio_sino -- the data term of a sinogram OSEM subset update
- * (paper Sec. 3: OSEM subset update of a span-1 subset sinogram; Sec. 5:
+ * (paper Sec. 2.6: OSEM subset update of a span-1 subset sinogram; Sec. 4:
  * emission and contamination sinograms), elementwise over n sinogram
  * entries (LORs x TOF bins, any order shared by the arrays):
  *     q[i] = p[i] + c[i] > 0 ? y[i] / (p[i] + c[i]) : 0
@@ -309,9 +309,9 @@ int jp_osem_subset_tof_lm_dev(jp_plan p, int32_t f0, int32_t f1, float* x, const
                               float sens_scale, const float* b_dev, const jp_tof* t, void* stream);
 
 /*
- * Image-based resolution model H (paper Sec. 3: every listmode OSEM
+ * Image-based resolution model H (paper Sec. 2.6: every listmode OSEM
  * reconstruction applies a shift-invariant isotropic 3D Gaussian of 4.5 mm
- * FWHM in image space; Sec. 5: two such convolutions per subset).  The
+ * FWHM in image space; Sec. 4: two such convolutions per subset).  The
  * paper fixes no discretisation; this library uses: per axis a,
  * sigma_a = fwhm_mm[a] / sqrt(8 ln 2); taps = the Gaussian sampled at t*d_a
  * (d_a the voxel size) for |t| <= R_a = ceil(truncate * sigma_a / d_a),
@@ -343,7 +343,7 @@ int jp_gauss3d(const float* img, float* out, float* work, int32_t n_images, cons
 /*
  * jp_osem_subset_tof_lm_ex -- listmode OSEM subset update, general form:
  *   x[j] <- sens[j] > 0 ? x[j] * (H^T A_S^T (1 / (A_S H x + b)))[j] / (sens[j] * sens_scale) : 0
- * with the resolution model H of r (paper Sec. 3), or H = identity when r
+ * with the resolution model H of r (paper Sec. 2.6), or H = identity when r
  * is NULL; sens is then the caller's H^T A^T 1.  Plan, frame range and TOF
  * rules as jp_osem_subset_tof_lm; b_dev non-NULL reads b from device memory
  * and the event range from the plan's device offsets (CUDA-graph

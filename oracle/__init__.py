@@ -1,5 +1,5 @@
 """FP64 CPU oracle for Joseph forward/back projection (paper Sec. 2.1-2.2),
-listmode OSEM and the image-based resolution model (Sec. 2.6, 3).
+listmode OSEM and the image-based resolution model (Sec. 2.6, 3, 4).
 
 TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
 the CPU-baseline leg of ``bench.py`` may import or run anything in this

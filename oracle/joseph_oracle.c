@@ -24,7 +24,7 @@
  *      c = t_s D + delta (delta: optional per-LOR TOF centre offset).  An
  *      optional per-LOR sigma replaces s for that LOR (per-event TOF
  *      resolution);
- *   5b. tabulated kernel (Sec. 5: a 1D lookup table permits non-Gaussian
+ *   5b. tabulated kernel (Sec. 4: a 1D lookup table permits non-Gaussian
  *      TOF kernels): with a table of n values at d_e = -h + e 2h/(n-1), the
  *      weight at d = tau - c is the linear interpolation of the table, and 0
  *      when |d| > h (replacing the Gaussian and its truncation);

@@ -60,9 +60,9 @@ def lm_osem(xs, xe, tof_bin, geom, tof, sens, b, n_iter, n_sub, threads=1, x0=No
 
 
 def sino_osem_subset_update(x, xs, xe, y, c, sens, geom, mode="nontof", tof=None, threads=1):
-    """One sinogram OSEM subset update (paper Sec. 3: an OSEM subset update
+    """One sinogram OSEM subset update (paper Sec. 2.6: an OSEM subset update
     with 34 subsets of equally spaced views; the emission and contamination
-    sinograms of Sec. 5).  For the subset's LORs (xs, xe), emission counts y
+    sinograms of Sec. 4).  For the subset's LORs (xs, xe), emission counts y
     and additive contamination c (both [n] non-TOF or [n, n_bins] TOF
     sinogram) and subset sensitivity sens = A_S^T 1:
         x <- x / sens * A_S^T ( y / (A_S x + c) ),   x = 0 where sens = 0,

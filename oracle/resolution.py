@@ -1,9 +1,9 @@
 """FP64 image-based resolution model.  TEST INFRASTRUCTURE ONLY (see the
 package docstring).
 
-Paper Sec. 3 (listmode OSEM set-up): every listmode OSEM reconstruction
+Paper Sec. 2.6 (listmode OSEM set-up): every listmode OSEM reconstruction
 models the scanner resolution with a shift-invariant, isotropic 3D Gaussian
-of 4.5 mm FWHM applied in image space; Sec. 5 counts two such convolutions
+of 4.5 mm FWHM applied in image space; Sec. 4 counts two such convolutions
 per subset (one before the forward projection, one after the back
 projection).  The paper does not fix the discretisation; this module reads it
 as follows (the same reading the CUDA path implements):

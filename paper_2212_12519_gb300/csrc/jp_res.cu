@@ -1,6 +1,6 @@
-// Image-based resolution model (paper Sec. 3: a shift-invariant isotropic 3D
+// Image-based resolution model (paper Sec. 2.6: a shift-invariant isotropic 3D
 // Gaussian of 4.5 mm FWHM applied in image space in every listmode OSEM
-// reconstruction; Sec. 5: two convolutions per subset became the bottleneck
+// reconstruction; Sec. 4: two convolutions per subset became the bottleneck
 // once the projectors were fast).
 //
 // The Gaussian is separable, so H is three 1D correlations, one kernel per

@@ -1,7 +1,7 @@
 """Listmode OSEM on the GPU (paper Sec. 2.6 and 3: TOF listmode OSEM,
 x <- x / s_sub * A_S^T (1 / (A_S x + b)), subsets of the event stream).
 
-With the image-based resolution model of Sec. 3 (a 3D Gaussian of
+With the image-based resolution model of Sec. 2.6 (a 3D Gaussian of
 ``fwhm_mm``, 4.5 mm in the paper) the projector is A H and the update
 x <- x / s'_sub * H^T A_S^T (1 / (A_S H x + b)) uses s' = H^T A^T 1
 (``resolution_sensitivity``); one call of jp_osem_subset_tof_lm_ex runs both

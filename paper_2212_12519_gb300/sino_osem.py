@@ -1,5 +1,5 @@
-"""Sinogram OSEM on the GPU (paper Sec. 3: OSEM subset updates with 34
-subsets of equally spaced views of a span-1 sinogram; Sec. 5: the emission
+"""Sinogram OSEM on the GPU (paper Sec. 2.6: OSEM subset updates with 34
+subsets of equally spaced views of a span-1 sinogram; Sec. 4: the emission
 sinogram, its forward projection and the additive contamination sinogram are
 held in device memory).
 

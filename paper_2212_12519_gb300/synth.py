@@ -64,7 +64,7 @@ class TofParams:
     sigma (mm), truncation in sigmas, number of sinogram TOF bins.
 
     ``kernel`` optionally replaces the Gaussian by a tabulated bin response
-    (Sec. 5: a 1D lookup table for non-Gaussian TOF kernels): the values at
+    (Sec. 4: a 1D lookup table for non-Gaussian TOF kernels): the values at
     the distances -h + e 2h / (len - 1) from the bin centre, h =
     ``kernel_half_width``, linearly interpolated, 0 beyond h."""
 
@@ -149,7 +149,7 @@ class SinoSpec:
 
     def subset(self, m: int, n_sub: int) -> "SinoSpec":
         """Views m, m + n_sub, m + 2 n_sub, ... of this sinogram's views: the
-        equally spaced view subsets of sinogram OSEM (paper Sec. 3)."""
+        equally spaced view subsets of sinogram OSEM (paper Sec. 2.6)."""
         return SinoSpec(self.scanner, self.n_views, self.n_rad, self.view_step * n_sub,
                         self.view_start + m * self.view_step)
 
@@ -176,7 +176,7 @@ def sinogram_lors(spec: SinoSpec, device="cpu", plane_range: Optional[Tuple[int,
     Mapping (view v, radial index rho in [-(n_rad-1)/2, (n_rad-1)/2]):
     c1 = (v + floor(rho/2)) mod n_c, c2 = (v - ceil(rho/2) + n_c/2) mod n_c;
     plane = r1 * n_rings + r2 over all ring pairs.  ``order`` names the flat
-    memory order from the slowest to the fastest axis (paper Sec. 3): "PVR"
+    memory order from the slowest to the fastest axis (paper Sec. 2.6): "PVR"
     (default) is plane-major, then view, then radial (radial fastest); "VRP"
     has the plane fastest and the view slowest; "RVP" the radial slowest and
     the plane fastest.  Returns float32 (xs, xe) [n, 3].  ``plane_range``
@@ -205,7 +205,7 @@ def sinogram_lors(spec: SinoSpec, device="cpu", plane_range: Optional[Tuple[int,
 
 def symmetry_axis(geom: "ImageGeom", xs: torch.Tensor, xe: torch.Tensor, axis: int):
     """Places the scanner's axial direction (z) on image axis ``axis`` (paper
-    Sec. 3, "symmetry axis" 0/1/2; 2 = axial fastest in memory, the default
+    Sec. 2.6, "symmetry axis" 0/1/2; 2 = axial fastest in memory, the default
     of the other generators): permutes the image geometry and the LOR
     coordinates alike, so projections equal those of axis 2 up to the voxel
     permutation.  Returns (geom, xs, xe)."""

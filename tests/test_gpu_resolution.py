@@ -1,4 +1,4 @@
-"""GPU image-based resolution model (separable 3D Gaussian, paper Sec. 3)
+"""GPU image-based resolution model (separable 3D Gaussian, paper Sec. 2.6)
 against the FP64 oracle's direct 3D correlation, and listmode OSEM with the
 resolution model against the oracle OSEM.
 

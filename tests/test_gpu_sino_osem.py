@@ -1,7 +1,7 @@
 """GPU sinogram OSEM (34-style view subsets, emission + contamination
-sinograms; paper Sec. 3 and 5) against the FP64 oracle update, and the
+sinograms; paper Sec. 2.6 and 4) against the FP64 oracle update, and the
 layout independence of the binned projector (sinogram orders PVR / VRP /
-RVP, image symmetry axis 0 / 1 / 2; paper Sec. 3)."""
+RVP, image symmetry axis 0 / 1 / 2; paper Sec. 2.6)."""
 import numpy as np
 import pytest
 import torch

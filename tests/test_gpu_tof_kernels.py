@@ -1,5 +1,5 @@
 """Tabulated (non-Gaussian) TOF kernels and per-event TOF sigma (paper
-Sec. 5: a 1D lookup table permits non-Gaussian kernels; listmode events
+Sec. 4: a 1D lookup table permits non-Gaussian kernels; listmode events
 with their own TOF resolution) against the FP64 oracle: planned (shared-
 memory table / exact per-event erf) and planless paths, TOF sinogram and
 listmode, forward element by element and back projection."""

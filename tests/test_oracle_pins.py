@@ -534,7 +534,7 @@ def test_planted_mistakes_are_caught():
 
 
 # ---------------------------------------------------------------------------
-# image-based resolution model (paper Sec. 3: 3D Gaussian, 4.5 mm FWHM)
+# image-based resolution model (paper Sec. 2.6: 3D Gaussian, 4.5 mm FWHM)
 # ---------------------------------------------------------------------------
 RES_FWHM = 4.5
 # voxels fine enough that the sampled Gaussian keeps the continuous moments
@@ -650,7 +650,7 @@ def test_osem_with_resolution_model():
 
 
 # ---------------------------------------------------------------------------
-# sinogram OSEM (paper Sec. 3: subset update with emission and contamination
+# sinogram OSEM (paper Sec. 2.6 and 4: subset update with emission and contamination
 # sinograms)
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("mode", ["nontof", "tof_sino"])
@@ -686,7 +686,7 @@ def test_sino_osem_fixed_point_and_counts(mode):
 
 
 # ---------------------------------------------------------------------------
-# tabulated (non-Gaussian) TOF kernels and per-LOR sigma (paper Sec. 5)
+# tabulated (non-Gaussian) TOF kernels and per-LOR sigma (paper Sec. 4)
 # ---------------------------------------------------------------------------
 def _tof_ext_pins(mutant=0):
     """Pins of the tabulated-kernel and per-LOR-sigma paths; returns the
