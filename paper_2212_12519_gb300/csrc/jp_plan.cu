@@ -50,6 +50,11 @@ struct KeyParams {
   const int64_t* frame_off;
   int n_frames;
   DevGeom g;
+  // per principal axis a: the in-plane axis b of the slope / offset keys (the
+  // longer of the two others, so that slope and offset follow the image's
+  // wide in-plane direction whichever axis holds the scanner's axial one);
+  // the axial-offset key takes the remaining axis c = 3 - a - b
+  int kb[3];
   int slope_bins, offset_bins, window_bins, zoff_bins, keys_per_frame;
   float tof_width;  // > 0: listmode window binning
   int keep_order;
@@ -88,7 +93,7 @@ __global__ void key_kernel(KeyParams p, uint32_t* __restrict__ keys, uint32_t* _
     lor_endpoints(p, j, xs, xe);
     const float d0 = xe[0] - xs[0], d1 = xe[1] - xs[1], d2 = xe[2] - xs[2];
     const int a = principal_axis(xs, xe);
-    const int b = (a == 0) ? 1 : 0;
+    const int b = p.kb[a];
     const DevGeom& g = p.g;
     const float da = sel3(a, d0, d1, d2), db = sel3(b, d0, d1, d2);
     const float sb = (da != 0.f) ? db / da : 0.f;  // in [-1, 1]
@@ -116,7 +121,7 @@ __global__ void key_kernel(KeyParams p, uint32_t* __restrict__ keys, uint32_t* _
     }
     int qz = 0;
     if (p.zoff_bins > 1) {
-      const int c = (a == 2) ? 1 : 2;
+      const int c = 3 - a - b;
       const int nc = sel3(c, g.n[0], g.n[1], g.n[2]);
       const float oc = sel3(c, g.o[0], g.o[1], g.o[2]), ivc = sel3(c, g.inv_v[0], g.inv_v[1], g.inv_v[2]);
       const float mc = 0.5f * (sel3(c, xs[0], xs[1], xs[2]) + sel3(c, xe[0], xe[1], xe[2]));
@@ -351,6 +356,11 @@ int bind(jp_plan p, const float* xs, const float* xe, const int16_t* tof_bin, co
   kp.dxyz = det ? det->xyz : nullptr; kp.n_det = det ? det->n_det : 0;
   kp.tof_bin = tof_bin; kp.delta = delta; kp.n = n;
   kp.frame_off = p->frame_off_dev; kp.n_frames = n_frames; kp.g = g;
+  for (int a = 0; a < 3; ++a) {
+    const int b0 = (a == 0) ? 1 : 0, b1 = (a == 2) ? 1 : 2;
+    const double e0 = (double)g.n[b0] * g.v[b0], e1 = (double)g.n[b1] * g.v[b1];
+    kp.kb[a] = (e1 > e0) ? b1 : b0;
+  }
   kp.slope_bins = p->dims.slope_bins; kp.offset_bins = p->dims.offset_bins;
   kp.window_bins = p->dims.window_bins; kp.zoff_bins = p->dims.zoff_bins;
   kp.keys_per_frame = p->dims.keys_per_frame;
