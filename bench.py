@@ -957,7 +957,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=200)
-    ap.add_argument("--serving-rates", default="0.5,1.0,1.5")
+    ap.add_argument("--serving-rates", default="0.5,0.8,1.0,1.5")
     ap.add_argument("--workload", default="tof_lm",
                     choices=["tof_lm", "nontof_lm", "sino_small", "sino_clinical", "tof_sino", "osem",
                              "sino_osem", "layout_study", "lm_osem_iter", "profile_case", "profile_osem",
