@@ -200,6 +200,13 @@ def run_ours(args):
         del p0
     x = W["x"].clone().requires_grad_(True)
     stream = torch.cuda.current_stream()
+    sigma_e = None
+    if args.event_sigma and not nontof:
+        # per-event TOF resolution: three timing classes around the scanner's
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(4998 + rank)
+        cls = torch.randint(0, 3, (n_total,), generator=gen, device=dev)
+        sigma_e = (tof.sigma * torch.tensor([0.85, 1.0, 1.2], device=dev)[cls]).float().contiguous()
 
     timers = {"fwd": [], "back": [], "bin": []}
 
@@ -235,6 +242,8 @@ def run_ours(args):
                                                         tof_bin=W["tb"]))
         else:
             ops.jp_plan_rebind_det(plan, W["ds"], W["de"], W["det"], W["offsets"], tof_bin=W["tb"])
+        if sigma_e is not None:
+            ops.jp_plan_set_event_sigma(plan, sigma_e)
         x.grad = None
         if record:
             p = TimedTOFLM.apply(x)
@@ -314,7 +323,8 @@ def run_ours(args):
             "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{'nontof' if nontof else 'tof'}_lm_batch{n_frames}x{epf // 1_000_000}M_200x200x71",
+            "config": {"workload": f"{'nontof' if nontof else 'tof'}_lm_batch{n_frames}x{epf // 1_000_000}M_200x200x71"
+                                   + ("_event_sigma" if sigma_e is not None else ""),
                        "frames_per_gpu": n_frames, "events_per_frame": epf, "image": list(g.shape),
                        "tof_bins": 0 if nontof else tof.n_bins,
                        "input": "listmode as recorded: int32 detector-index pairs"
@@ -968,6 +978,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--serving-slots", type=int, default=4)
     ap.add_argument("--fwhm", type=float, default=4.5, help="OSEM resolution model FWHM in mm (0: none)")
+    ap.add_argument("--event-sigma", action="store_true",
+                    help="listmode workload with per-event TOF sigma (three timing classes)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
