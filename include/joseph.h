@@ -353,7 +353,7 @@ int jp_gauss3d(const float* img, float* out, float* work, int32_t n_images, cons
  *         image-sized build, clear and fold per call);
  *         JP_OSEM_PATH_DIRECT: forward from the image, back projection by
  *         scalar atomics into an image (no quad traffic; cheaper for
- *         subsets of fewer than about nvox / 20 events, measured on GB300
+ *         subsets of fewer than about nvox / 24 events, measured on GB300
  *         for 128x128x71 and 200x200x71 images);
  *         JP_OSEM_PATH_AUTO: DIRECT when b_dev is NULL and the subset holds
  *         fewer than nvox / JP_OSEM_DIRECT_VOXELS_PER_EVENT events, else
@@ -366,7 +366,7 @@ int jp_gauss3d(const float* img, float* out, float* work, int32_t n_images, cons
 #define JP_OSEM_PATH_AUTO 0
 #define JP_OSEM_PATH_QUADS 1
 #define JP_OSEM_PATH_DIRECT 2
-#define JP_OSEM_DIRECT_VOXELS_PER_EVENT 20
+#define JP_OSEM_DIRECT_VOXELS_PER_EVENT 24
 int jp_osem_subset_tof_lm_ex(jp_plan p, int32_t f0, int32_t f1, float* x, const float* sens,
                              float sens_scale, float b, const float* b_dev, const jp_tof* t,
                              const jp_resolution* r, int32_t path, float* work, void* stream);

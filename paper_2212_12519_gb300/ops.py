@@ -27,7 +27,7 @@ JP_PLAN_KEEP_ORDER = 1
 JP_PLAN_TOF_EXACT = 2
 JP_PLAN_INTERLEAVED = 4
 OSEM_PATHS = {"auto": 0, "quads": 1, "direct": 2}
-OSEM_DIRECT_VOXELS_PER_EVENT = 20  # JP_OSEM_DIRECT_VOXELS_PER_EVENT
+OSEM_DIRECT_VOXELS_PER_EVENT = 24  # JP_OSEM_DIRECT_VOXELS_PER_EVENT
 
 
 class JosephError(RuntimeError):
