@@ -362,23 +362,25 @@ def run_ours(args):
 def run_e2e(args, W, plan, g, tof, dev, ws, nontof=False):
     """Same step through the public API with the inputs copied from pinned
     host memory and the loss and gradient images read back, every step.
-    Two device buffer sets: step k+1's inputs are copied on a side stream
-    while step k computes (and step k's results are read back on it), so the
-    copies overlap the compute; the timed region holds all of them."""
+    NB device buffer sets (--e2e-buffers): the inputs of step k + NB - 1 are
+    copied on a side stream while steps k .. k + NB - 2 compute (and step
+    k's results are read back on it), so the copies overlap the compute and
+    a copy may take up to NB - 1 steps; the timed region holds all of them."""
     from paper_2212_12519_gb300 import ops
     from paper_2212_12519_gb300.autograd import JosephNonTOF, JosephTOFLM, PoissonLogLik
     keys = ("ds", "de", "det", "w", "bframe", "x") if nontof else ("ds", "de", "det", "tb", "w", "bframe", "x")
     host = {k: W[k].cpu().pin_memory() for k in keys}
-    dbuf = [{k: torch.empty_like(W[k]) for k in keys} for _ in range(2)]
-    out_grad = [torch.empty(W["x"].shape, dtype=torch.float32).pin_memory() for _ in range(2)]
-    out_loss = [torch.empty((), dtype=torch.float64).pin_memory() for _ in range(2)]
+    nb = max(2, int(args.e2e_buffers))
+    dbuf = [{k: torch.empty_like(W[k]) for k in keys} for _ in range(nb)]
+    out_grad = [torch.empty(W["x"].shape, dtype=torch.float32).pin_memory() for _ in range(nb)]
+    out_loss = [torch.empty((), dtype=torch.float64).pin_memory() for _ in range(nb)]
     h2d = sum(v.numel() * v.element_size() for v in host.values())
     d2h = out_grad[0].numel() * 4 + 8
     comp = torch.cuda.current_stream()
     copy = torch.cuda.Stream()
-    copied = [torch.cuda.Event() for _ in range(2)]
-    done = [torch.cuda.Event() for _ in range(2)]
-    results = [None, None]
+    copied = [torch.cuda.Event() for _ in range(nb)]
+    done = [torch.cuda.Event() for _ in range(nb)]
+    results = [None] * nb
 
     def h2d_into(b):
         with torch.cuda.stream(copy):
@@ -403,12 +405,12 @@ def run_e2e(args, W, plan, g, tof, dev, ws, nontof=False):
             out_loss[b].copy_(results[b][1], non_blocking=True)
 
     def run(nsteps):
-        h2d_into(0)
+        for k in range(min(nb - 1, nsteps)):
+            h2d_into(k)
         for k in range(nsteps):
-            b = k % 2
-            if k + 1 < nsteps:
-                h2d_into(1 - b)
-            compute(b)
+            if k + nb - 1 < nsteps:
+                h2d_into((k + nb - 1) % nb)  # the set step k - 1 used
+            compute(k % nb)
         comp.wait_stream(copy)
 
     for e in done:
@@ -425,7 +427,7 @@ def run_e2e(args, W, plan, g, tof, dev, ws, nontof=False):
     ms = t0.elapsed_time(t1) / n
     return {"value": W["xs"].shape[0] * ws / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
             "steps": n, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-            "copies": "pinned host <-> device every step, overlapped with compute (2 buffer sets)"}
+            "copies": f"pinned host <-> device every step, overlapped with compute ({nb} buffer sets)"}
 
 
 # ---------------------------------------------------------------------------
@@ -964,6 +966,8 @@ def main():
     ap.add_argument("--ref-events", type=int, default=400_000)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-buffers", type=int, default=3,
+                    help="device input buffer sets of the end-to-end pipeline (>= 2)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=200)
