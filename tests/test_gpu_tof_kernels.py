@@ -156,6 +156,33 @@ def test_osem_per_event_sigma_vs_oracle(ops, path):
     assert rel_l2(x.cpu().numpy(), x_or) <= 1e-4
 
 
+@pytest.mark.parametrize("bin_width,sigma,n_bins", [(9.0, 7.0, 15), (10.0, 9.9667, 9), (4.0, 7.0, 25),
+                                                     (9.0, 7.0, 3), (9.0, 7.0, 1), (30.0, 2.0, 7)])
+def test_tof_sino_bin_windows(ops, bin_width, sigma, n_bins):
+    """Gaussian TOF sinograms whose plane samples reach 1 to 12 bins (2 R / w
+    from 1.4 to 11.5, the bin-aligned table), with TOF centre offsets and
+    LORs in both directions; few bins (the window clipped at both ends) and
+    a single bin."""
+    xs, xe = lors(20_000, seed=7460)
+    n = len(xs)
+    rng = np.random.Generator(np.random.PCG64(7461))
+    img = rng.uniform(0, 3, size=GEOM.shape).astype(np.float32)
+    tof = synth.TofParams(bin_width=bin_width, sigma=sigma, n_sigmas=3.0, n_bins=n_bins)
+    delta = rng.normal(0, 3, size=n).astype(np.float32)
+    p_or, amb = oracle.fwd(xs, xe, img, GEOM, "tof_sino", tof, delta=delta, threads=THREADS, amb_eps=AMB_EPS,
+                           return_amb=True)
+    y = rng.uniform(0, 1, size=(n, n_bins)).astype(np.float32)
+    b_or = oracle.back(xs, xe, y, GEOM, "tof_sino", tof, delta=delta, threads=THREADS)
+    plan = ops.jp_plan_create(cuda(xs), cuda(xe), GEOM, delta=cuda(delta))
+    p = ops.jp_fwd_tof_sino(plan, cuda(img), tof)
+    out = torch.zeros(GEOM.shape, device="cuda")
+    ops.jp_back_tof_sino(plan, cuda(y), tof, out)
+    torch.cuda.synchronize()
+    assert fwd_err(p.cpu().numpy(), p_or, amb) <= FWD_TOL
+    assert rel_l2(out.cpu().numpy(), b_or) <= BACK_TOL
+    plan.destroy()
+
+
 @pytest.mark.parametrize("table", ["box2", "max_nodes"])
 def test_tabulated_kernel_extremes(ops, table):
     """The smallest table (2 nodes: a box, value 1 up to the support edge)
