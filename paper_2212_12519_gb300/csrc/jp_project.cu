@@ -323,7 +323,11 @@ __global__ void __launch_bounds__(kMaxBlock) planned_kernel(const ProjParams p) 
           const float w = fminf(fmaxf(fmaf(kk, r.dw, r.wc), -1.f), wb);
           const float fu = floorf(u), fw = floorf(w);
           const float al = u - fu, be = w - fw;
-          const float4 v = __ldg(Q + quad_index(p.kfast, k, (int)fu + 1, (int)fw + 1, na, nb2, nc2));
+          // TOF listmode: the lanes' windows start on different planes, so
+          // the quads rarely hit L1 (10%); loads cached in L2 only skip the
+          // L1 fills (forward 5.18 vs 5.26 ms on a 40M-event frame)
+          const float4* qa = Q + quad_index(p.kfast, k, (int)fu + 1, (int)fw + 1, na, nb2, nc2);
+          const float4 v = (MODE == 2) ? __ldcg(qa) : __ldg(qa);
           const float top = fmaf(be, v.z - v.x, v.x);
           const float bot = fmaf(be, v.w - v.y, v.y);
           const float s = fmaf(al, bot - top, top);
