@@ -1,17 +1,23 @@
 // Joseph forward and back projection kernels (paper Sec. 2.1, 2.2).
 //
-// One thread follows one LOR plane by plane along its principal axis
-// (steps a2-a6 of the hot path):
+// A thread, or a group of G lanes, follows one LOR plane by plane along its
+// principal axis (steps a2-a6 of the hot path; the planless kernels, one
+// thread per LOR in caller order, read and add the 4 voxels directly):
 //   a2  per-LOR setup (exact principal axis, plane range, affine maps in
 //       voxel units anchored at the centre plane so every sample is one FMA
 //       from a small anchor value, never a long running sum);
-//   a3  forward: bilinear interpolation of the 4 nearest voxels through
-//       read-only (L1/L2-resident) loads, summed and scaled by v_a / cos_a;
-//   a4  TOF weights as differences of erff at the bin edges (a TOF sinogram
-//       shares each inner edge between two neighbouring bins, so W bins cost
-//       W+1 erff; listmode evaluates only the planes of its TOF window);
+//   a3  forward: bilinear interpolation of the 4 nearest voxels, one
+//       16-byte load of a zero-padded quad image per sample (L2-resident),
+//       summed and scaled by v_a / cos_a;
+//   a4  TOF weights, the difference of erff at the bin edges, by default
+//       read from a shared-memory table of exact erf differences with
+//       linear interpolation (a caller's table of a non-Gaussian kernel the
+//       same way), or with erff itself (a TOF sinogram then shares each
+//       inner edge between two neighbouring bins, so W bins cost W+1 erff);
+//       listmode evaluates only the planes of its TOF window;
 //   a5  back projection: the transposed coefficients scattered with
-//       fire-and-forget atomic adds (RED) into the image;
+//       fire-and-forget reductions (RED): one 16-byte vector reduction per
+//       sample into the quad images, folded into the image afterwards;
 //   a6  planned calls read LORs in binned order and scatter/gather the
 //       projection values through the plan's permutation.
 #include <cuda_runtime.h>
