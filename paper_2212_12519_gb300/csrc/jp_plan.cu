@@ -4,13 +4,15 @@
 // report up to 7.6x run-time spread across memory orders (Sec. 3), traced to
 // races and cache behaviour (Sec. 4), and suggest pre-sorting events (Sec. 4).
 // Here each LOR gets a key
-//     frame | principal axis a | slope d_b/d_a | in-plane offset u at the
-//     centre plane | (listmode) TOF window centre along a
-// and a counting sort (histogram, exclusive scan, scatter) reorders the LORs
-// so that the 32 lanes of a warp follow nearly parallel, nearby rays whose
-// samples differ mainly along axis c -- the fastest-varying image axis for
-// a in {0,1}.  The sorted LORs are packed as two float4 (xs, delta) and
-// (xe, tof_bin) for 16-byte coalesced loads; perm maps back to caller order.
+//     frame | principal axis a | slope d_b/d_a | offset along b at the
+//     centre plane | (listmode) TOF window centre along a | offset along c
+//     at the centre plane
+// (b the longer in-plane axis of a, c the other one) and a counting sort
+// (histogram, exclusive scan, scatter) reorders the LORs so that the 32
+// lanes of a warp follow nearly parallel, nearby rays.  The sorted LORs are
+// packed as two float4, (xs, delta or the caller index) and (xe, tof_bin),
+// for 16-byte coalesced loads; with TOF centre offsets perm maps back to
+// caller order, otherwise the caller index in the record does.
 #include <cuda_runtime.h>
 
 #include <algorithm>
