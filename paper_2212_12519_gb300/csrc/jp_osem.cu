@@ -1,6 +1,7 @@
-// Listmode OSEM element-wise kernels (step a8; paper Sec. 2.6 and 3:
-// x <- x / s_sub * A_S^T (1 / (A_S x + b))) and an FP64 reduction used only
-// for the sensitivity-normalisation check.
+// OSEM element-wise kernels: listmode (step a8; paper Sec. 2.6 and 3:
+// x <- x / s_sub * A_S^T (1 / (A_S x + b))) and the sinogram data term
+// y / (A_m x + c) (Sec. 2.6), plus an FP64 reduction used only for the
+// sensitivity-normalisation check.
 #include <cuda_runtime.h>
 
 #include "jp_internal.cuh"
