@@ -1,7 +1,10 @@
 // OSEM element-wise kernels: listmode (step a8; paper Sec. 2.6 and 3:
 // x <- x / s_sub * A_S^T (1 / (A_S x + b))) and the sinogram data term
-// y / (A_m x + c) (Sec. 2.6), plus an FP64 reduction used only for the
-// sensitivity-normalisation check.
+// y / (A_m x + c) (Sec. 2.6); the Poisson log-likelihood loss of a
+// listmode batch and its gradient with respect to the projections; an FP64
+// reduction used only for the sensitivity-normalisation check; and the
+// microbenchmark of the L2 vector-reduction ceiling that the back
+// projection's roofline is measured against.
 #include <cuda_runtime.h>
 
 #include "jp_internal.cuh"
