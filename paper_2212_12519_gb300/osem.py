@@ -23,7 +23,7 @@ can be captured once into a CUDA graph and replayed.
 from __future__ import annotations
 
 from dataclasses import dataclass
-from typing import Dict, Optional, Tuple
+from typing import Optional, Tuple
 
 import torch
 

@@ -19,7 +19,7 @@ Workloads (the paper's benchmark shapes, Sec. 2.6, rebuilt on synthetic data):
 from __future__ import annotations
 
 import math
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 from typing import Optional, Sequence, Tuple
 
 import numpy as np

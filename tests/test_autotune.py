@@ -1,6 +1,5 @@
 """Autotuner host logic (CPU, fake timer) and, on the GPU, that the chosen
 options keep parity with the oracle."""
-import numpy as np
 import pytest
 import torch
 

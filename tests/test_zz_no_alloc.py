@@ -3,7 +3,6 @@ allocate device memory, e.g. inside a graph capture or under a fixed memory
 budget) gives the same image as the allocating planless entry point, on two
 calls in a row (its fixed workspace is reused and must be cleared), and
 rejects images larger than its fixed workspace."""
-import numpy as np
 import pytest
 import torch
 
