@@ -157,12 +157,14 @@ def test_osem_per_event_sigma_vs_oracle(ops, path):
 
 
 @pytest.mark.parametrize("bin_width,sigma,n_bins", [(9.0, 7.0, 15), (10.0, 9.9667, 9), (4.0, 7.0, 25),
-                                                     (9.0, 7.0, 3), (9.0, 7.0, 1), (30.0, 2.0, 7)])
+                                                     (9.0, 7.0, 3), (9.0, 7.0, 1), (30.0, 2.0, 7),
+                                                     (1.0, 1.0, 128)])
 def test_tof_sino_bin_windows(ops, bin_width, sigma, n_bins):
     """Gaussian TOF sinograms whose plane samples reach 1 to 12 bins (2 R / w
     from 1.4 to 11.5, the bin-aligned table), with TOF centre offsets and
-    LORs in both directions; few bins (the window clipped at both ends) and
-    a single bin."""
+    LORs in both directions; few bins (the window clipped at both ends), a
+    single bin, and the most bins a sinogram may have (JP_MAX_TOF_BINS, whose
+    per-thread accumulators cap the forward's block size)."""
     xs, xe = lors(20_000, seed=7460)
     n = len(xs)
     rng = np.random.Generator(np.random.PCG64(7461))
@@ -213,7 +215,8 @@ def test_tabulated_kernel_argument_checks(ops):
     plan = ops.jp_plan_create(cuda(xs), cuda(xe), GEOM)
     img = torch.zeros(GEOM.shape, device="cuda")
     bad = [synth.TofParams.tabulated(9.0, 13, [1.0] * 4, 0.0),          # half width 0
-           synth.TofParams.tabulated(9.0, 13, [1.0] * 2049, 10.0)]      # more nodes than the table holds
+           synth.TofParams.tabulated(9.0, 13, [1.0] * 2049, 10.0),      # more nodes than the table holds
+           synth.TofParams(bin_width=1.0, sigma=1.0, n_sigmas=3.0, n_bins=129)]  # above JP_MAX_TOF_BINS
     for tof in bad:
         with pytest.raises(ops.JosephError):
             ops.jp_fwd_tof_sino(plan, img, tof)
