@@ -216,11 +216,27 @@ int jp_plan_destroy(jp_plan p);
 int jp_plan_info(jp_plan p, int64_t* n_lor, int32_t* n_frames, int32_t* perm_out, void* stream);
 
 /*
- * Planned projections.  img / img_accum: device float32 images, frame f at
- * offset f*img_stride elements (img_stride = 0: every frame uses the same
- * image).  proj: caller order, float32 [n_total] or [n_total][N] (TOF sino).
+ * Planned projections (paper Sec. 2.1-2.2): forward proj = A img, back
+ * img_accum += A^T proj, non-TOF, TOF sinogram (all N bins of a LOR in one
+ * traversal) or TOF listmode (the event's bin only, over its TOF window).
+ *   img / img_accum  device float32 images, frame f at offset f*img_stride
+ *                    elements (img_stride = 0: every frame uses the same
+ *                    image); the back projection accumulates (the caller
+ *                    zeroes img_accum)
+ *   proj             device float32 in caller order, [n_total] or
+ *                    [n_total][N] (TOF sinogram, bin fastest); the forward
+ *                    overwrites it
+ *   t                TOF parameters (host struct; a tabulated kernel's table
+ *                    is a device pointer)
  * TOF listmode calls need a plan created with tof_bin; delta comes from the
- * plan (0 if it was created without tof_center_offset).
+ * plan (0 if it was created without tof_center_offset).  All pointers are
+ * the caller's; the calls allocate nothing and run asynchronously on
+ * `stream`.  One plan must not run two calls at once (its workspace is
+ * shared).
+ * Errors: JP_ERR_ARG (NULL plan or arrays, img_stride < 0 or smaller than
+ * one image with per-frame images, invalid TOF parameters), JP_ERR_ALIGN
+ * (arrays not 4-byte aligned), JP_ERR_STATE (TOF listmode without tof_bin,
+ * per-event sigma with a TOF sinogram), JP_ERR_CUDA.
  */
 int jp_fwd(jp_plan p, const float* img, int64_t img_stride, float* proj, void* stream);
 int jp_back(jp_plan p, const float* proj, float* img_accum, int64_t img_stride, void* stream);
@@ -379,6 +395,7 @@ int jp_osem_subset_tof_lm_ex(jp_plan p, int32_t f0, int32_t f1, float* x, const 
  * w may be NULL (all ones); b is device float [n_frames] with b_f the
  * background of event e's frame (frames from the plan's offsets in caller
  * order; plan NULL: one frame); scale is a device double or NULL (1).
+ * Errors: JP_ERR_ARG, JP_ERR_ALIGN, JP_ERR_CUDA.
  */
 int jp_poisson_loglik_value(jp_plan p, const float* proj, const float* w, const float* b, int64_t n,
                             double* value, void* stream);
