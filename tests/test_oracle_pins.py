@@ -685,6 +685,75 @@ def test_sino_osem_fixed_point_and_counts(mode):
     assert np.all(np.isfinite(x2)) and np.all(x2 == 0.0)
 
 
+def _osem_pins(mutant=0):
+    """Fast versions of the OSEM and gradient pins above, run against a
+    (possibly mutated) oracle; returns the names of the pins that failed."""
+    failed = []
+    close = lambda a, b: abs(a - b) <= 1e-12 * max(abs(b), 1e-300)  # noqa: E731
+    # listmode OSEM: count preservation with and without background, and
+    # through the resolution model
+    g, tof, _, xs, xe, tb = _small_lm_problem(n_events=1200, seed=97)
+    rng = np.random.Generator(np.random.PCG64(98))
+    sens = rng.uniform(0.5, 2.0, size=g.shape)
+    n_sub, m = 4, 1
+    x0 = rng.uniform(0.2, 1.5, size=g.shape)
+    sub = slice(m, None, n_sub)
+    p = oracle.fwd(xs[sub], xe[sub], x0, g, "tof_lm", tof, tof_bin=tb[sub])
+    for b in (0.7, 0.0):
+        x1 = oracle.lm_osem_subset_update(x0, xs, xe, tb, g, tof, sens, b, m, n_sub, _mutant=mutant)
+        want = float(np.sum(p / (p + b))) if b else float(np.sum(p > 0))
+        if not close(float(np.sum(sens / n_sub * x1)), want):
+            failed.append(f"lm-counts-b{b}")
+    ph = oracle.fwd(xs[sub], xe[sub], oracle.gauss3d(x0, g, 4.5), g, "tof_lm", tof, tof_bin=tb[sub])
+    x1 = oracle.lm_osem_subset_update(x0, xs, xe, tb, g, tof, sens, 0.4, m, n_sub, fwhm_mm=4.5, _mutant=mutant)
+    if not close(float(np.sum(sens / n_sub * x1)), float(np.sum(ph / (ph + 0.4)))):
+        failed.append("lm-res-counts")
+    # sinogram OSEM: fixed point of consistent data, count preservation
+    g2 = G((10, 9, 7), (-4.5, -4.0, -3.3), (1.0, 1.1, 1.2))
+    xs2, xe2 = synth.random_lors(200, g2, seed=143)
+    x = rng.uniform(0.2, 1.5, size=g2.shape)
+    p2 = oracle.fwd(xs2, xe2, x, g2)
+    c = rng.uniform(0.05, 0.3, size=p2.shape)
+    s2 = oracle.back(xs2, xe2, np.ones_like(p2), g2)
+    pos = s2 > 0
+    x_fp = oracle.sino_osem_subset_update(x, xs2, xe2, p2 + c, c, s2, g2, _mutant=mutant)
+    if np.abs(x_fp[pos] - x[pos]).max() > 1e-12 * x.max():
+        failed.append("sino-fixed-point")
+    y = rng.poisson(p2 + c).astype(np.float64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        x1 = oracle.sino_osem_subset_update(x, xs2, xe2, y, c, s2, g2, _mutant=mutant)
+    if not (np.all(np.isfinite(x1)) and close(float(np.sum(s2 * x1)), float(np.sum(p2 * y / (p2 + c))))):
+        failed.append("sino-counts")
+    # gradient of the listmode log-likelihood against central differences
+    xg = x0 + 0.1
+    w = rng.uniform(0.5, 1.5, size=400)
+    b = 0.3
+    _, grad = oracle.poisson_loglik_grad(xg, xs[:400], xe[:400], tb[:400], g, tof, w, b, _mutant=mutant)
+    h = 1e-6
+    for j in rng.choice(xg.size, size=8, replace=False):
+        e = np.zeros(xg.size)
+        e[j] = h
+        e = e.reshape(xg.shape)
+        pp = oracle.fwd(xs[:400], xe[:400], xg + e, g, "tof_lm", tof, tof_bin=tb[:400])
+        pm = oracle.fwd(xs[:400], xe[:400], xg - e, g, "tof_lm", tof, tof_bin=tb[:400])
+        fd = float(np.sum(w * np.log1p((pp - pm) / (pm + b)))) / (2 * h)
+        gj = grad.reshape(-1)[j]
+        if abs(fd - gj) > 1e-7 * max(abs(gj), 1e-3 * np.abs(grad).max()):
+            failed.append("grad-fd")
+            break
+    return failed
+
+
+def test_osem_planted_mistakes_are_caught():
+    """Each plausible mistake in the OSEM and gradient oracles fails at least
+    one pin: sensitivity not divided by n_sub, background dropped, a
+    contiguous block as the subset, H^T not applied, contamination dropped,
+    the ratio inverted, the weights dropped from the gradient."""
+    assert _osem_pins(0) == []
+    for mutant in range(1, 8):
+        assert _osem_pins(mutant), f"OSEM mutant {mutant} passed every pin"
+
+
 # ---------------------------------------------------------------------------
 # tabulated (non-Gaussian) TOF kernels and per-LOR sigma (paper Sec. 4)
 # ---------------------------------------------------------------------------
