@@ -43,6 +43,10 @@ BACK_DRAM_BYTES_PER_EVENT = (608_469_248 + 76_418_304) / 10_000_000
 # non-TOF sinogram back projection (group kernel, plane-fastest quads):
 # l1tex reduction sectors / plane samples on the 266k-LOR small sinogram
 SINO_BACK_SECTORS_PER_SAMPLE = 6_298_790 / 8_856_832
+# TOF sinogram kernels (planned, bin-aligned weight table): warp instructions
+# per plane sample, ncu smsp__inst_executed / plane samples on a
+# 2,028,240-LOR view subset of the clinical TOF sinogram
+TOF_SINO_WARP_INSTR_PER_SAMPLE = {"fwd": 1_212_321_753 / 266_701_248, "back": 1_592_531_301 / 266_701_248}
 
 
 # ---------------------------------------------------------------------------
@@ -449,6 +453,22 @@ SINO_WORKLOADS = {
 }
 
 
+def issue_roofline(dom, samples, kernel_ms, clk, dev):
+    """TOF sinogram kernels are bound by instruction issue (about 7 TOF bins
+    per plane sample, each a table read, an interpolation and an
+    accumulation): achieved warp instructions/s against 4 schedulers per SM
+    issuing one warp instruction per cycle each at the sampled SM clock."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
+    peak = sms * 4 * float(mhz) * 1e6
+    wi = TOF_SINO_WARP_INSTR_PER_SAMPLE[dom]
+    achieved = samples * wi / (kernel_ms / 1e3)
+    return {"kernel": f"{dom}_tof_sino", "resource": "instruction issue", "bound": "alu",
+            "achieved": achieved, "peak": peak, "unit": "warp instructions/s", "frac": achieved / peak,
+            "warp_instructions_per_sample": wi, "clock_mhz": float(mhz),
+            "instructions_source": "ncu smsp__inst_executed / plane samples, 2.03M-LOR view subset"}
+
+
 def run_sino(args):
     """One step = forward + back projection of every LOR of the sinogram
     (LOR endpoints and their plan are computed once, outside the timed
@@ -542,9 +562,7 @@ def run_sino(args):
                  "reductions_per_s": samples / (kern["back"] / 1e3),
                  "sectors_per_reduction": SINO_BACK_SECTORS_PER_SAMPLE,
                  "sectors_source": "ncu l1tex red sectors / plane samples, 266k-LOR small sinogram"}
-                if not is_tof else
-                {"kernel": "back_tof_sino", "resource": "issue / ALU (about 7 TOF bin weights per sample)",
-                 "note": "no single memory resource binds; see DESIGN kernels table"}),
+                if not is_tof else issue_roofline(dom, samples, kern[dom], clk, dev)),
             "clocks": clk, "gpu_launches": int(launches)}
     if not args.no_cpu_baseline:
         import oracle
