@@ -155,8 +155,18 @@ static double tof_w(const tof_t* t, double tau, double centre, double sigma) {
 static double tof_weight_amb(double tau, double centre, const tof_t* t, double sigma, int* amb) {
   double dist = tau - centre;
   double r = t->table ? t->table_hw : t->n_sigmas * sigma + 0.5 * t->bin_width;
+#if OR_MUTANT == 10
+  /* planted: every sample inside the window flagged, not only the edge band */
+  *amb = fabs(dist) <= r + t->amb_eps;
+#else
   *amb = fabs(fabs(dist) - r) <= t->amb_eps;
+#endif
   if (fabs(dist) > r && !*amb) return 0.0;
+#if OR_MUTANT == 12
+  /* planted: the truncated weight (0 just outside the edge) instead of the
+   * untruncated one */
+  if (fabs(dist) > r) return 0.0;
+#endif
   if (t->table) return table_value(t, dist);
   double k = 1.0 / (sqrt(2.0) * sigma);
   double g = 0.5 * (erf((dist + 0.5 * t->bin_width) * k) - erf((dist - 0.5 * t->bin_width) * k));
@@ -307,7 +317,10 @@ static void fwd_one(const double* xs, const double* xe, const geom_t* g, const t
   }
   for (int q = 0; q < nout; ++q) {
     out[q] *= r.w0;
+#if OR_MUTANT != 11
+    /* (planted mistake 11 leaves the ambiguity magnitude unscaled) */
     if (amb) amb[q] *= r.w0;
+#endif
   }
 }
 

@@ -8,7 +8,7 @@ import torch
 
 import oracle
 from paper_2212_12519_gb300 import synth
-from _parity import AMB_EPS, BACK_TOL, FWD_TOL, fwd_err, rel_l2
+from _parity import AMB_EPS, BACK_TOL, FWD_TOL, amb_check, fwd_err, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -119,6 +119,7 @@ def test_tof_sino(ops, clinical_img, planned):
         p = ops.jp_fwd_lors(cuda(xs), cuda(xe), cuda(clinical_img), g, "tof_sino", tof)
         ops.jp_back_lors(cuda(xs), cuda(xe), cuda(y), g, out, "tof_sino", tof)
     torch.cuda.synchronize()
+    amb_check(amb, xs, xe, g, tof, np.abs(clinical_img).max())
     assert fwd_err(p.cpu().numpy(), p_or, amb) <= FWD_TOL
     assert rel_l2(out.cpu().numpy(), b_or) <= BACK_TOL
 
@@ -155,6 +156,7 @@ def test_tof_lm(ops, clinical_img, lm_events, planned):
         p = ops.jp_fwd_lors(cuda(xs), cuda(xe), cuda(clinical_img), g, "tof_lm", tof, tof_bin=dtb)
         ops.jp_back_lors(cuda(xs), cuda(xe), cuda(y), g, out, "tof_lm", tof, tof_bin=dtb)
     torch.cuda.synchronize()
+    amb_check(amb, xs, xe, g, tof, np.abs(clinical_img).max())
     assert fwd_err(p.cpu().numpy(), p_or, amb) <= FWD_TOL
     assert rel_l2(out.cpu().numpy(), b_or) <= BACK_TOL
 
@@ -195,6 +197,8 @@ def test_tof_offsets_and_nonisotropic(ops):
             p = ops.jp_fwd_tof_lm(plan, cuda(img), tof)
             ops.jp_back_tof_lm(plan, dy, tof, out)
         torch.cuda.synchronize()
+        if t is not None:
+            amb_check(amb, xs, xe, g, t, np.abs(img).max())
         assert fwd_err(p.cpu().numpy(), p_or, amb) <= FWD_TOL, mode
         assert rel_l2(out.cpu().numpy(), b_or) <= BACK_TOL, mode
 
@@ -249,6 +253,7 @@ def test_batched_frames(ops, clinical_img, lm_events):
             continue
         p_or, amb = oracle.fwd(xs[a:b], xe[a:b], imgs[f], g, "tof_lm", tof, tof_bin=tb[a:b],
                                threads=THREADS, amb_eps=AMB_EPS, return_amb=True)
+        amb_check(amb, xs[a:b], xe[a:b], g, tof, np.abs(imgs[f]).max())
         assert fwd_err(p[a:b], p_or, amb) <= FWD_TOL
         b_or = oracle.back(xs[a:b], xe[a:b], ys[a:b], g, "tof_lm", tof, tof_bin=tb[a:b], threads=THREADS)
         assert rel_l2(out[f], b_or) <= BACK_TOL
@@ -256,9 +261,10 @@ def test_batched_frames(ops, clinical_img, lm_events):
     cuts2 = [0, 10_000, 130_000]
     ops.jp_plan_rebind(plan, cuda(xs[:cuts2[-1]]), cuda(xe[:cuts2[-1]]), cuts2, tof_bin=cuda(tb[:cuts2[-1]]))
     p2 = ops.jp_fwd_tof_lm(plan, cuda(imgs[:2]), tof).cpu().numpy()
-    p_or0 = oracle.fwd(xs[:10_000], xe[:10_000], imgs[0], g, "tof_lm", tof, tof_bin=tb[:10_000],
-                       threads=THREADS)
-    assert fwd_err(p2[:10_000], p_or0) <= 2 * FWD_TOL
+    p_or0, amb0 = oracle.fwd(xs[:10_000], xe[:10_000], imgs[0], g, "tof_lm", tof, tof_bin=tb[:10_000],
+                             threads=THREADS, amb_eps=AMB_EPS, return_amb=True)
+    amb_check(amb0, xs[:10_000], xe[:10_000], g, tof, np.abs(imgs[0]).max())
+    assert fwd_err(p2[:10_000], p_or0, amb0) <= FWD_TOL
 
 
 @pytest.mark.parametrize("lpw", [0, 4, 32])
@@ -325,6 +331,8 @@ def test_degenerate_axes(ops, shape):
             p = ops.jp_fwd_tof_lm(plan, cuda(img), tof)
         q = ops.jp_fwd_lors(cuda(xs), cuda(xe), cuda(img), g, mode, t, tof_bin=cuda(tb) if mode == "tof_lm" else None)
         torch.cuda.synchronize()
+        if t is not None:
+            amb_check(amb, xs, xe, g, t, np.abs(img).max())
         assert fwd_err(p.cpu().numpy(), p_or, amb) <= FWD_TOL, mode
         assert fwd_err(q.cpu().numpy(), p_or, amb) <= FWD_TOL, mode
         nout = tof.n_bins if mode == "tof_sino" else 1
@@ -376,12 +384,15 @@ def test_detector_index_plans(ops, clinical_img):
     p_or, amb = oracle.fwd(xs.numpy()[:50_000][ok[:50_000]], xe.numpy()[:50_000][ok[:50_000]], clinical_img, g,
                            "tof_lm", tof, tof_bin=tb.numpy()[:50_000][ok[:50_000]], threads=THREADS,
                            amb_eps=AMB_EPS, return_amb=True)
+    amb_check(amb, xs.numpy()[:50_000][ok[:50_000]], xe.numpy()[:50_000][ok[:50_000]], g, tof,
+              np.abs(clinical_img).max())
     assert fwd_err(fd[:50_000][~bad[:50_000]].cpu().numpy(), p_or, amb) <= FWD_TOL
     # rebind to the second half of the events as one frame
     ops.jp_plan_rebind_det(pd, ds.cuda()[60_000:], de.cuda()[60_000:], table, tof_bin=tb.cuda()[60_000:])
     f2 = ops.jp_fwd_tof_lm(pd, img, tof).cpu().numpy()
     p_or2, amb2 = oracle.fwd(xs.numpy()[60_000:], xe.numpy()[60_000:], clinical_img, g, "tof_lm", tof,
                              tof_bin=tb.numpy()[60_000:], threads=THREADS, amb_eps=AMB_EPS, return_amb=True)
+    amb_check(amb2, xs.numpy()[60_000:], xe.numpy()[60_000:], g, tof, np.abs(clinical_img).max())
     assert fwd_err(f2, p_or2, amb2) <= FWD_TOL
     pd.destroy()
     pc.destroy()

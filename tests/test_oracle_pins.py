@@ -856,3 +856,107 @@ def test_tabulated_and_sigma_planted_mistakes():
     for mutant in (8, 9):
         oracle.joseph.build(mutant)
         assert _tof_ext_pins(mutant), f"planted mistake {mutant} not caught"
+
+
+# ---------------------------------------------------------------------------
+# the TOF-edge ambiguity output (reading r1 of the truncation rule, Sec. 2.1
+# and 2.6): per output, w0 * sum over the samples whose |tau - c| lies within
+# amb_eps of the truncation radius R of |untruncated weight * sample value|
+# ---------------------------------------------------------------------------
+def _gauss_bin_raw(dist, D, s):
+    k = 1.0 / (math.sqrt(2.0) * s)
+    return 0.5 * (math.erf((dist + 0.5 * D) * k) - math.erf((dist - 0.5 * D) * k))
+
+
+def _amb_by_tent(xs, xe, img, geom, tof, eps, centres):
+    """Independent restatement: for LOR r and each TOF centre in
+    centres[r], visit the planes inside the segment, interpolate with tent
+    functions, flag samples with ||tau - c| - R| <= eps."""
+    n, o, v = geom.shape, geom.origin, geom.voxsize
+    R = tof.n_sigmas * tof.sigma + 0.5 * tof.bin_width
+    out = []
+    for p, q, cs in zip(np.asarray(xs, np.float64), np.asarray(xe, np.float64), centres):
+        d = q - p
+        L = math.sqrt(float(np.dot(d, d)))
+        a = _principal_axis_exact(p, q)
+        b, c = [i for i in range(3) if i != a]
+        w0 = v[a] * L / abs(d[a])
+        row = np.zeros(len(cs))
+        for k in range(n[a]):
+            X = o[a] + k * v[a]
+            if not (min(p[a], q[a]) <= X <= max(p[a], q[a])):
+                continue
+            t = (X - p[a]) / d[a]
+            u = (p[b] + t * d[b] - o[b]) / v[b]
+            w = (p[c] + t * d[c] - o[c]) / v[c]
+            s = 0.0
+            for ib in range(n[b]):
+                for ic in range(n[c]):
+                    tt = _tent(u - ib) * _tent(w - ic)
+                    if tt:
+                        ijk = [0, 0, 0]
+                        ijk[a], ijk[b], ijk[c] = k, ib, ic
+                        s += tt * img[tuple(ijk)]
+            tau = (t - 0.5) * L
+            for m, cen in enumerate(cs):
+                if abs(abs(tau - cen) - R) <= eps:
+                    row[m] += w0 * abs(_gauss_bin_raw(tau - cen, tof.bin_width, tof.sigma) * s)
+        out.append(row)
+    return np.array(out)
+
+
+def _amb_pins(mutant=0):
+    """Returns the names of the ambiguity pins that fail."""
+    failed = []
+    # (1) an axis-aligned ray along axis 0 through voxel centres, with dyadic
+    #     coordinates: tau_k = 2k - 8 exactly, R = 3 * 2 + 4 / 2 = 8, so plane
+    #     0 sits at the window edge of bin centre delta; the sample value is
+    #     f[0, 1, 2] and w0 = v_0 = 2
+    g = G((8, 4, 4), (0.0, 0.0, 0.0), (2.0, 2.0, 2.0))
+    tof = T(bin_width=4.0, sigma=2.0, n_sigmas=3.0, n_bins=3)
+    rng = np.random.Generator(np.random.PCG64(171))
+    f = rng.uniform(0.5, 1.5, size=g.shape)
+    a, b = (-8.0, 2.0, 4.0), (24.0, 2.0, 4.0)
+    eps = 1e-3
+    for delta, inside_band in ((0.0, True), (5e-4, True), (-5e-4, True), (1.5e-3, False), (-1.5e-3, False)):
+        _, amb = oracle.fwd([a], [b], f, g, "tof_lm", tof, tof_bin=[0], delta=[delta], amb_eps=eps,
+                            return_amb=True, mutant=mutant)
+        expect = 2.0 * abs(_gauss_bin_raw(-8.0 - delta, 4.0, 2.0) * f[0, 1, 2]) if inside_band else 0.0
+        if inside_band and abs(amb[0] - expect) > 1e-12 * expect:
+            failed.append(f"edge-value({delta})")
+        if not inside_band and amb[0] != 0.0:
+            failed.append(f"outside-band({delta})")
+    # (2) the same ray as a 3-bin TOF sinogram: centres -4, 0, 4 put planes
+    #     6, 0 and 2 on the edges of bins 0, 1 and 2
+    _, amb = oracle.fwd([a], [b], f, g, "tof_sino", tof, amb_eps=eps, return_amb=True, mutant=mutant)
+    gedge = _gauss_bin_raw(8.0, 4.0, 2.0)
+    expect = [2.0 * gedge * f[6, 1, 2], 2.0 * gedge * f[0, 1, 2], 2.0 * gedge * f[2, 1, 2]]
+    if np.abs(amb[0] - expect).max() > 1e-12 * max(expect):
+        failed.append("sino-edges")
+    # (3) random oblique LORs with a wide band (0.3 mm) so that both cases
+    #     occur: the output equals the independent tent-function restatement,
+    #     and is exactly 0 where no sample falls in the band
+    g3 = G((6, 5, 4), (-2.6, -1.9, -1.4), (1.0, 0.9, 0.8))
+    t3 = T(bin_width=1.1, sigma=0.9, n_sigmas=2.0, n_bins=5)
+    xs, xe = synth.random_lors(40, synth.ImageGeom(g3.shape, g3.origin, g3.voxsize), seed=172, radius_factor=1.4)
+    x3 = rng.uniform(0.2, 1.2, size=g3.shape)
+    tb = rng.integers(-2, 3, size=len(xs))
+    de = rng.uniform(-0.4, 0.4, size=len(xs))
+    _, amb = oracle.fwd(xs, xe, x3, g3, "tof_lm", t3, tof_bin=tb, delta=de, amb_eps=0.3, return_amb=True,
+                        mutant=mutant)
+    ref = _amb_by_tent(xs, xe, x3, g3, t3, 0.3, [[tb[i] * t3.bin_width + de[i]] for i in range(len(xs))])[:, 0]
+    if np.any((ref == 0.0) != (amb == 0.0)) or np.abs(amb - ref).max() > 1e-12 * max(ref.max(), 1e-30):
+        failed.append("random-vs-tent")
+    if not (0 < np.count_nonzero(ref) < len(ref)):
+        failed.append("random-cases")
+    return failed
+
+
+def test_tof_edge_ambiguity_pins():
+    assert _amb_pins() == []
+
+
+def test_tof_edge_ambiguity_planted_mistakes():
+    for mutant in (10, 11, 12):
+        oracle.joseph.build(mutant)
+        assert _amb_pins(mutant), f"planted ambiguity mistake {mutant} not caught"
