@@ -122,6 +122,15 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def plan_opts(args) -> dict:
+    """Plan options from the command line (0 = the library default)."""
+    o = dict(tile_lors=args.tile_lors, block=args.block, max_ctas_per_sm=args.ctas_per_sm,
+             lors_per_warp=args.lors_per_warp)
+    if args.path == "tiles":
+        o["tiles"] = True
+    return o
+
+
 # ---------------------------------------------------------------------------
 # workload
 # ---------------------------------------------------------------------------
@@ -187,18 +196,20 @@ def run_ours(args):
     if nontof:
         # same events without their TOF bins
         W["tb"] = None
-    opts = {}
+    opts = plan_opts(args)
     if not args.no_autotune:
         from paper_2212_12519_gb300 import autotune
         if args.workload == "nontof_lm":
             opts = autotune.tune(W["xs"][:epf], W["xe"][:epf], g, mode="nontof")
         else:
             opts = autotune.tune(W["xs"][:epf], W["xe"][:epf], g, mode="tof_lm", tof=tof, tof_bin=W["tb"][:epf])
+    if args.path == "tiles":
+        opts = dict(opts, tiles=True)
     plan = ops.jp_plan_create_batch_det(W["ds"], W["de"], W["det"], g, W["offsets"], tof_bin=W["tb"],
                                         tof_bin_width=0.0 if nontof else tof.bin_width, **opts)
     if nontof:
         # background: 10 % of each frame's mean non-TOF projection
-        p0 = ops.jp_fwd(plan, W["x"]).view(n_frames, epf).double().mean(dim=1)
+        p0 = ops.jp_fwd(plan, W["x"]).view(n_frames, epf).mean(dim=1)
         W["bvals"] = [float(0.1 * v) for v in p0.cpu()]
         W["bframe"] = torch.tensor(W["bvals"], dtype=torch.float32, device=dev)
         del p0
@@ -378,9 +389,9 @@ def run_e2e(args, W, plan, g, tof, dev, ws, nontof=False):
     nb = max(2, int(args.e2e_buffers))
     dbuf = [{k: torch.empty_like(W[k]) for k in keys} for _ in range(nb)]
     out_grad = [torch.empty(W["x"].shape, dtype=torch.float32).pin_memory() for _ in range(nb)]
-    out_loss = [torch.empty((), dtype=torch.float64).pin_memory() for _ in range(nb)]
+    out_loss = [torch.empty((), dtype=torch.float32).pin_memory() for _ in range(nb)]
     h2d = sum(v.numel() * v.element_size() for v in host.values())
-    d2h = out_grad[0].numel() * 4 + 8
+    d2h = out_grad[0].numel() * 4 + 4
     comp = torch.cuda.current_stream()
     copy = torch.cuda.Stream()
     copied = [torch.cuda.Event() for _ in range(nb)]
@@ -492,7 +503,7 @@ def run_sino(args):
         y = torch.poisson(torch.full((n, tof.n_bins), 2.0, device=dev), generator=gen)
     else:
         y = torch.rand(n, generator=gen, device=dev)
-    plan = ops.jp_plan_create(xs, xe, g)
+    plan = ops.jp_plan_create(xs, xe, g, **plan_opts(args))
     out = torch.zeros(g.shape, device=dev)
     stream = torch.cuda.current_stream()
     tim = {"fwd": [], "back": []}
@@ -748,9 +759,7 @@ def run_layout_study(args):
 
 
 # ---------------------------------------------------------------------------
-# small case for ncu captures: one frame of --events TOF listmode events
-# (launch order: plan [key, scan x3, scatter, flags], then twice
-# [quad build, forward, quad zero, back, fold-back], then a rebind)
+# small cases for ncu captures
 # ---------------------------------------------------------------------------
 def run_profile_osem(args):
     """One frame (--events events, 200x200x71), one iteration of 34 subsets
@@ -802,6 +811,9 @@ def run_profile_tof_sino(args):
 
 
 def run_profile_case(args):
+    """One frame of --events TOF listmode events (200x200x71): the plan
+    (key, scan x3, scatter, flags), then three times forward + back
+    projection (each timed with CUDA events), then a rebind."""
     from paper_2212_12519_gb300 import build as jbuild, ops, synth
     jbuild.build()
     ops.load()
@@ -811,13 +823,21 @@ def run_profile_case(args):
     xs, xe, tb = synth.lm_events(ph, g, synth.SCANNER_CLINICAL, tof, args.events, seed=4051, device=dev)
     y = torch.rand(args.events, device=dev)
     img = torch.zeros(g.shape, device=dev)
-    plan = ops.jp_plan_create(xs, xe, g, tof_bin=tb, tof_bin_width=tof.bin_width)
-    for _ in range(2):
-        ops.jp_fwd_tof_lm(plan, ph, tof)
-        ops.jp_back_tof_lm(plan, y, tof, img)
+    popts = plan_opts(args)
+    plan = ops.jp_plan_create(xs, xe, g, tof_bin=tb, tof_bin_width=tof.bin_width, **popts)
+    ms = {"fwd": [], "back": []}
+    for _ in range(3):
+        for name, fn in (("fwd", lambda: ops.jp_fwd_tof_lm(plan, ph, tof)),
+                         ("back", lambda: ops.jp_back_tof_lm(plan, y, tof, img))):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            ms[name].append((a, b))
     ops.jp_plan_rebind(plan, xs, xe, tof_bin=tb)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_case": "tof_lm", "events": args.events,
+    print(json.dumps({"profile_case": "tof_lm", "events": args.events, "path": args.path, "plan_opts": popts,
+                      "ms": {k: [a.elapsed_time(b) for a, b in v] for k, v in ms.items()},
                       "samples": ops.jp_count_samples(plan, "tof_lm", tof)}))
     plan.destroy()
 
@@ -1008,6 +1028,12 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--serving-slots", type=int, default=4)
     ap.add_argument("--fwhm", type=float, default=4.5, help="OSEM resolution model FWHM in mm (0: none)")
+    ap.add_argument("--path", default="quads", choices=["quads", "tiles"],
+                    help="projection kernels of sorted plans: quad images or shared-memory tiles")
+    ap.add_argument("--tile-lors", type=int, default=0, help="plan option: LORs per tile (0 = default)")
+    ap.add_argument("--block", type=int, default=0, help="plan option: threads per CTA (0 = default)")
+    ap.add_argument("--ctas-per-sm", type=int, default=0, help="plan option: resident CTAs per SM (0 = default)")
+    ap.add_argument("--lors-per-warp", type=int, default=0, help="plan option: LORs per warp (0 = default)")
     ap.add_argument("--event-sigma", action="store_true",
                     help="listmode workload with per-event TOF sigma (three timing classes)")
     args = ap.parse_args()

@@ -119,6 +119,8 @@ typedef struct {
   int32_t max_ctas_per_sm;/* cap on the resident CTAs per SM of the persistent
                              projection kernels, leaving room for work on other
                              streams (0 = as many as fit) */
+  int32_t tile_lors;      /* LORs per tile of the shared-memory tile kernels
+                             (JP_PLAN_TILES; 0 = 256; 32..1024) */
 } jp_plan_opts;
 
 #define JP_PLAN_KEEP_ORDER 1
@@ -127,6 +129,28 @@ typedef struct {
                                   OSEM subsets); frame_offsets then only give
                                   offsets[n_frames] = n_total and all frames share
                                   one image */
+#define JP_PLAN_TILES 8        /* project through the shared-memory tiles (below)
+                                  instead of the quad images */
+
+/* Projection paths of a sorted plan (neither KEEP_ORDER nor INTERLEAVED).
+ * By default every call goes through zero-padded quad images, one per
+ * principal axis, holding the 4 bilinear neighbours of every sample
+ * position: a sample is one 16-byte load (forward) or one 16-byte vector
+ * reduction into L2 (back projection).
+ * JP_PLAN_TILES sends non-TOF and TOF-listmode calls with lors_per_warp 0, 1,
+ * 2, 4 or 8 through shared-memory tiles instead: a CTA takes up to
+ * tile_lors consecutive sorted LORs that share (frame, principal axis, slope
+ * bin, offset bin), i.e. cross the image close to one line, and holds the
+ * image voxels they reach in shared memory.  The back projection adds its
+ * samples there (fixed-point integer atomics, scaled per tile so that no
+ * cell can overflow; absolute error per sample <= sum over the tile of
+ * |w0 y g_max| / 2^31) and then adds the box into the image (the race-prone
+ * scatter of Sec. 2.2 privatised per CTA); the forward projection reads its
+ * samples from the box and equals the quad path's with the same lanes per
+ * LOR bit for bit.  32/lors_per_warp lanes (at least 4) walk one LOR.  On
+ * the clinical workloads this path cuts the L2 reductions per sample from
+ * ~0.73 sectors to ~0.23 but executes more instructions than it saves, and
+ * is slower; TOF-sinogram calls always use the quad images. */
 
 /* TOF weights in planned calls come by default from a table of the exact
  * erf difference at JP_TOF_TABLE nodes over [-R, R] (R = n_sigmas*sigma +
@@ -390,16 +414,22 @@ int jp_osem_subset_tof_lm_ex(jp_plan p, int32_t f0, int32_t f1, float* x, const 
 /*
  * Listmode Poisson log-likelihood of a forward projection p (the training
  * objective of unrolled reconstruction networks, paper Sec. 4):
- *   jp_poisson_loglik_value: *value (device double) = sum_e w_e log(p_e + b_f)
+ *   jp_poisson_loglik_value: *value (device float) = sum_e w_e log(p_e + b_f)
  *   jp_poisson_loglik_grad:  grad_e = scale * w_e / (p_e + b_f)
  * w may be NULL (all ones); b is device float [n_frames] with b_f the
  * background of event e's frame (frames from the plan's offsets in caller
- * order; plan NULL: one frame); scale is a device double or NULL (1).
+ * order; plan NULL: one frame); scale is a device float or NULL (1).
+ * The value is an FP32 compensated sum (error-free TwoSum steps, error of
+ * order eps * sum_e |w_e log(p_e + b_f)| whatever n is) in two passes: block
+ * partial sums go to work, device float[2 * JP_LOGLIK_BLOCKS] (8-byte
+ * aligned, caller-owned scratch, contents undefined afterwards), and one
+ * block adds them up.  Calls sharing a work buffer must not overlap.
  * Errors: JP_ERR_ARG, JP_ERR_ALIGN, JP_ERR_CUDA.
  */
+#define JP_LOGLIK_BLOCKS 1024
 int jp_poisson_loglik_value(jp_plan p, const float* proj, const float* w, const float* b, int64_t n,
-                            double* value, void* stream);
-int jp_poisson_loglik_grad(jp_plan p, const float* proj, const float* w, const float* b, const double* scale,
+                            float* value, float* work, void* stream);
+int jp_poisson_loglik_grad(jp_plan p, const float* proj, const float* w, const float* b, const float* scale,
                            int64_t n, float* grad, void* stream);
 
 /* listmode OSEM start image: x[j] = sens[j] > 0 ? 1 : 0 for nvox voxels */

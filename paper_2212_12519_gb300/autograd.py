@@ -67,7 +67,7 @@ def nontof_project(x, plan):
 
 
 class PoissonLogLik(torch.autograd.Function):
-    """L = sum_e w_e log(p_e + b_f) for listmode projections p (FP64 sum),
+    """L = sum_e w_e log(p_e + b_f) for listmode projections p (FP32 compensated sum),
     value and gradient each in one pass of the library's kernels; b holds one
     background per frame of ``plan`` (or one value with plan None)."""
 
@@ -81,7 +81,7 @@ class PoissonLogLik(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gout):
         (p,) = ctx.saved_tensors
-        g = ops.jp_poisson_loglik_grad(ctx.plan, p, ctx.w, ctx.b, scale=gout.to(torch.float64).contiguous())
+        g = ops.jp_poisson_loglik_grad(ctx.plan, p, ctx.w, ctx.b, scale=gout.to(torch.float32).contiguous())
         return g, None, None, None
 
 

@@ -332,6 +332,7 @@ struct jp_plan_s {
   jp_plan_opts opts;
   jp::PlanDims dims;
   bool has_tof_bin, has_delta;
+  int kb[3];              // per principal axis: the in-plane axis of the slope / offset keys
   float4* lor;            // [2*capacity]: (xs, delta or caller index bits), (xe, tof_bin bits)
   int32_t* perm;          // [capacity] binned position -> caller index (used when delta is given;
                           // otherwise the caller index rides in the record's first .w)

@@ -7,6 +7,8 @@
 // projection's roofline is measured against.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "jp_internal.cuh"
 
 namespace jp {
@@ -46,30 +48,73 @@ __global__ void update_kernel(float* __restrict__ x, const float* __restrict__ b
   }
 }
 
+// Compensated FP32 summation: (s, c) carries the sum s + c; each addition
+// is an error-free TwoSum (Knuth) whose rounding error goes to c, so the
+// accumulated error is of order eps * sum |terms| with no growth in the
+// number of terms (cascaded summation, Rump, Ogita and Oishi).  The _rn
+// intrinsics keep the compiler from contracting or reassociating.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bv = __fsub_rn(s, a);
+  const float av = __fsub_rn(s, bv);
+  e = __fadd_rn(__fsub_rn(a, av), __fsub_rn(b, bv));
+}
+
+__device__ __forceinline__ void comp_merge(float& s, float& c, float s2, float c2) {
+  float t, e;
+  two_sum(s, s2, t, e);
+  s = t;
+  c = __fadd_rn(__fadd_rn(c, c2), e);
+}
+
+// block-wide compensated sum of (s, c); the result is valid in thread 0
+__device__ __forceinline__ void block_comp_sum(float& s, float& c) {
+  __shared__ float2 red[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    const float s2 = __shfl_down_sync(0xffffffffu, s, o);
+    const float c2 = __shfl_down_sync(0xffffffffu, c, o);
+    comp_merge(s, c, s2, c2);
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = make_float2(s, c);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const float2 v = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : make_float2(0.f, 0.f);
+    s = v.x;
+    c = v.y;
+    for (int o = 16; o > 0; o >>= 1) {
+      const float s2 = __shfl_down_sync(0xffffffffu, s, o);
+      const float c2 = __shfl_down_sync(0xffffffffu, c, o);
+      comp_merge(s, c, s2, c2);
+    }
+  }
+}
+
+// pass 1: each block's compensated partial sum of w_e log(p_e + b_f) into part[block]
 __global__ void loglik_value_kernel(const float* __restrict__ p, const float* __restrict__ w,
                                     const float* __restrict__ b, const int64_t* __restrict__ off, int n_frames,
-                                    int64_t n, double* out) {
-  __shared__ double red[32];
-  double s = 0.0;
+                                    int64_t n, float2* __restrict__ part) {
+  float s = 0.f, c = 0.f;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int f = (n_frames > 1) ? frame_of(off, n_frames, i) : 0;
     const float wi = w ? __ldcs(w + i) : 1.f;
-    s += (double)(wi * logf(__ldcs(p + i) + __ldg(b + f)));
+    comp_merge(s, c, __fmul_rn(wi, logf(__ldcs(p + i) + __ldg(b + f))), 0.f);
   }
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (threadIdx.x == 0) atomicAdd(out, s);
-  }
+  block_comp_sum(s, c);
+  if (threadIdx.x == 0) part[blockIdx.x] = make_float2(s, c);
+}
+
+// pass 2 (one block): the partials' compensated sum into *out
+__global__ void loglik_final_kernel(const float2* __restrict__ part, int nb, float* __restrict__ out) {
+  float s = 0.f, c = 0.f;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) comp_merge(s, c, part[i].x, part[i].y);
+  block_comp_sum(s, c);
+  if (threadIdx.x == 0) *out = __fadd_rn(s, c);
 }
 
 __global__ void loglik_grad_kernel(const float* __restrict__ p, const float* __restrict__ w,
                                    const float* __restrict__ b, const int64_t* __restrict__ off, int n_frames,
-                                   const double* __restrict__ scale, int64_t n, float* __restrict__ g) {
-  const float sc = scale ? (float)__ldg(scale) : 1.f;
+                                   const float* __restrict__ scale, int64_t n, float* __restrict__ g) {
+  const float sc = scale ? __ldg(scale) : 1.f;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int f = (n_frames > 1) ? frame_of(off, n_frames, i) : 0;
     const float wi = w ? __ldcs(w + i) : 1.f;
@@ -231,26 +276,35 @@ int loglik_common(jp_plan pl, const float* p, const float* w, const float* b, in
 }  // namespace
 
 extern "C" int jp_poisson_loglik_value(jp_plan pl, const float* p, const float* w, const float* b, int64_t n,
-                                       double* value, void* stream) {
+                                       float* value, float* work, void* stream) {
   clear_error();
-  if (!value || !aligned(value, 8)) return fail(JP_ERR_ARG, "value must be an aligned device double");
+  if (!value) return fail(JP_ERR_ARG, "value is NULL");
+  if (!work) return fail(JP_ERR_ARG, "work is NULL");
+  if (!aligned(value, 4) || !aligned(work, 8)) return fail(JP_ERR_ALIGN, "value / work misaligned");
   const int64_t* off;
   int nf;
   int rc = loglik_common(pl, p, w, b, n, &off, &nf);
   if (rc) return rc;
-  JP_TRY_CUDA(cudaMemsetAsync(value, 0, sizeof(double), (cudaStream_t)stream));
-  if (n == 0) return JP_OK;
-  loglik_value_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(p, w, b, off, nf, n, value);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (n == 0) {
+    JP_TRY_CUDA(cudaMemsetAsync(value, 0, sizeof(float), st));
+    return JP_OK;
+  }
+  const int nb = std::min(grid_for(n, 256), JP_LOGLIK_BLOCKS);
+  float2* part = reinterpret_cast<float2*>(work);
+  loglik_value_kernel<<<nb, 256, 0, st>>>(p, w, b, off, nf, n, part);
+  count_launch();
+  loglik_final_kernel<<<1, 1024, 0, st>>>(part, nb, value);
   count_launch();
   JP_TRY_CUDA(cudaGetLastError());
   return JP_OK;
 }
 
 extern "C" int jp_poisson_loglik_grad(jp_plan pl, const float* p, const float* w, const float* b,
-                                      const double* scale, int64_t n, float* grad, void* stream) {
+                                      const float* scale, int64_t n, float* grad, void* stream) {
   clear_error();
   if (n > 0 && !grad) return fail(JP_ERR_ARG, "grad is NULL");
-  if (!aligned(grad, 4) || !aligned(scale, 8)) return fail(JP_ERR_ALIGN, "misaligned array");
+  if (!aligned(grad, 4) || !aligned(scale, 4)) return fail(JP_ERR_ALIGN, "misaligned array");
   const int64_t* off;
   int nf;
   int rc = loglik_common(pl, p, w, b, n, &off, &nf);

@@ -362,6 +362,7 @@ int bind(jp_plan p, const float* xs, const float* xe, const int16_t* tof_bin, co
     const int b0 = (a == 0) ? 1 : 0, b1 = (a == 2) ? 1 : 2;
     const double e0 = (double)g.n[b0] * g.v[b0], e1 = (double)g.n[b1] * g.v[b1];
     kp.kb[a] = (e1 > e0) ? b1 : b0;
+    p->kb[a] = kp.kb[a];
   }
   kp.slope_bins = p->dims.slope_bins; kp.offset_bins = p->dims.offset_bins;
   kp.window_bins = p->dims.window_bins; kp.zoff_bins = p->dims.zoff_bins;
@@ -457,6 +458,8 @@ static int create_batch(jp_plan* out, const float* xs, const float* xe, const in
       o.lors_per_warp != 8 && o.lors_per_warp != 16 && o.lors_per_warp != 32)
     return fail(JP_ERR_ARG, "opts.lors_per_warp must be 0, 1, 2, 4, 8, 16 or 32");
   if (!(o.tof_bin_width >= 0.f) || !isfinite(o.tof_bin_width)) return fail(JP_ERR_ARG, "opts.tof_bin_width must be finite and >= 0");
+  if (o.tile_lors == 0) o.tile_lors = 256;
+  if (o.tile_lors < 32 || o.tile_lors > 1024) return fail(JP_ERR_ARG, "opts.tile_lors must be 0 or 32..1024");
   int window_bins = (o.tof_bin_width > 0.f && tof_bin) ? o.window_bins : 1;
   int64_t kpf = 3LL * o.slope_bins * o.offset_bins * window_bins * o.zoff_bins;
   if (o.flags & JP_PLAN_KEEP_ORDER) kpf = 1;

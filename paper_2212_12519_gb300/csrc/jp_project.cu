@@ -26,6 +26,7 @@
 #include <cstring>
 
 #include "jp_internal.cuh"
+#include "jp_proj.cuh"
 
 namespace jp {
 
@@ -111,152 +112,6 @@ int make_tof(const jp_tof* t, bool sino, DevTof* out) {
 }
 
 namespace {
-
-constexpr int kMaxBlock = 512;
-constexpr int kLut = JP_TOF_TABLE;  // table nodes over [-R, R]
-
-struct ProjParams {
-  // per-event TOF sigma in binned order (listmode), or nullptr
-  const float* sig;
-  // planned source
-  const float4* lor;
-  const int32_t* perm;
-  const int64_t* frame_off;
-  int n_frames;
-  // direct source
-  const float* xs;
-  const float* xe;
-  const int16_t* tof_bin;
-  const float* delta;
-  int64_t n;
-  int64_t img_stride;
-  DevGeom g;
-  DevTof tof;
-  const float* img_in;
-  float* proj_out;
-  const float* proj_in;
-  float* img_out;
-  // planned workspace
-  float4* quads;
-  QuadLayout ql;
-  const int32_t* axis_used;
-  int shared;  // all frames use one image (img_stride == 0)
-  int kfast;   // quad order: 1 plane-fastest, 0 plane-major
-  // listmode OSEM subset update
-  float4* quads_bp;   // back-projection quads (plane-fastest)
-  float bg;           // additive background b
-  const float* bg_ptr;  // or read from device memory when set
-  int f0, f1;         // OSEM: subset frames [f0, f1), range read from frame_off on the device
-  const float* sens;  // sensitivity image
-  float sens_scale;
-  int perm_in_rec;    // caller index in the first record's .w (no TOF centre offsets)
-  int max_per_sm;     // host side: cap on resident CTAs per SM for persistent launches (0 = occupancy)
-  // persistent kernels take chunks of LORs from this counter (reset by the
-  // workspace kernel launched just before them), so the chunks in flight
-  // stay a contiguous window of the binned order (one frame's image at a time)
-  unsigned int* counter;
-};
-
-__device__ __forceinline__ int frame_of(const int64_t* __restrict__ off, int n_frames, int64_t i) {
-  int lo = 0, hi = n_frames - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (__ldg(off + mid) <= i) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
-// ---------------------------------------------------------------------------
-// TOF weight table: node e at dist = -R + e h, h = 2R / (kLut - 1); entry e
-// holds (g_e, g_{e+1} - g_e) so a lookup is one 8-byte shared load and an FMA.
-// The nodes are exact erf differences; linear interpolation between them is
-// the table method of the TOF kernel mentioned in the paper's Sec. 4.
-// ---------------------------------------------------------------------------
-// With a tabulated kernel (T.user) the table holds the caller's T.nodes
-// nodes instead.  Entry nodes - 1 holds (g_last, 0), so a coordinate that
-// rounds to a hair above the last node needs no clamp of the fraction.
-__device__ void build_lut(float2* lut, const DevTof& T) {
-  if (T.user) {
-    for (int e = threadIdx.x; e < T.nodes - 1; e += blockDim.x) {
-      const float g0 = __ldg(T.user + e);
-      lut[e] = make_float2(g0, __ldg(T.user + e + 1) - g0);
-    }
-    if (threadIdx.x == 0) lut[T.nodes - 1] = make_float2(__ldg(T.user + T.nodes - 1), 0.f);
-    return;
-  }
-  const float h = 2.f * T.R / (float)(T.nodes - 1);
-  for (int e = threadIdx.x; e < T.nodes - 1; e += blockDim.x) {
-    float g0 = tof_g(fmaf((float)e, h, -T.R), T);
-    float g1 = tof_g(fmaf((float)(e + 1), h, -T.R), T);
-    lut[e] = make_float2(g0, g1 - g0);
-  }
-  if (threadIdx.x == 0) lut[T.nodes - 1] = make_float2(tof_g(T.R, T), 0.f);
-}
-
-// bin-aligned table (T.m > 0): node e at -Rp + e h, h = w / m, untruncated
-// erf differences (the bin selection applies the truncation), last entry
-// (g_last, 0)
-__device__ void build_lut_aligned(float2* lut, const DevTof& T) {
-  const float h = T.width / (float)T.m;
-  for (int e = threadIdx.x; e < T.nodes_a - 1; e += blockDim.x) {
-    const float g0 = tof_g(fmaf((float)e, h, -T.Rp), T);
-    const float g1 = tof_g(fmaf((float)(e + 1), h, -T.Rp), T);
-    lut[e] = make_float2(g0, g1 - g0);
-  }
-  if (threadIdx.x == 0) lut[T.nodes_a - 1] = make_float2(tof_g(T.Rp, T), 0.f);
-}
-
-// table value at the table coordinate xl = (dist + R) / h of a bin inside
-// the support (so xl is in [0, nodes - 1] up to rounding); the index clamp
-// only keeps the shared-memory read in bounds for any input
-__device__ __forceinline__ float lut_at(const float2* lut, float xl, int last) {
-  const int ix = min(max((int)xl, 0), last);
-  const float2 e = lut[ix];
-  return fmaf(xl - (float)ix, e.y, e.x);
-}
-
-// x is clamped to [0, nodes - 1] and the last interval also serves x =
-// nodes - 1 (fraction 1), so the end nodes are reproduced exactly
-__device__ __forceinline__ float lut_g(const float2* lut, float dist, const DevTof& T) {
-  float x = (dist + T.R) * T.inv_h;
-  x = fminf(fmaxf(x, 0.f), (float)(T.nodes - 1));
-  const int ix = min((int)x, T.nodes - 2);
-  float fr = x - (float)ix;
-  float2 e = lut[ix];
-  return fmaf(fr, e.y, e.x);
-}
-
-// k_e: 1 / (sqrt2 sigma) of the LOR (its own sigma with per-event TOF
-// resolution, else T.k); the shared-memory table holds T's sigma only, so a
-// per-event sigma takes the exact path
-template <bool LUT>
-__device__ __forceinline__ float tof_weight(const float2* lut, float dist, const DevTof& T, float k_e) {
-  if (LUT) return lut_g(lut, dist, T);
-  if (T.user) return user_g(dist, T);
-  return 0.5f * (erff((dist + T.half) * k_e) - erff((dist - T.half) * k_e));
-}
-
-__device__ __forceinline__ bool slot_axis_used(const int32_t* used, int slot, int a, int shared, int n_frames) {
-  if (!shared) return __ldg(used + 3 * slot + a) != 0;
-  for (int f = 0; f < n_frames; ++f)
-    if (__ldg(used + 3 * f + a)) return true;
-  return false;
-}
-
-// TOF resolution of binned listmode LOR i: k = 1 / (sqrt2 sigma) and the
-// support half-width R, from its own sigma when the plan has per-event sigma
-// (a value <= 0 keeps the scalar one; a tabulated kernel ignores sigma)
-__device__ __forceinline__ void event_tof(const ProjParams& p, int64_t i, float& k, float& R) {
-  k = p.tof.k;
-  R = p.tof.R;
-  if (p.sig && !p.tof.user) {
-    const float s = __ldg(p.sig + i);
-    if (s > 0.f) {
-      k = 1.0f / (1.41421356237309515f * s);
-      R = fmaf(p.tof.ns, s, p.tof.half);
-    }
-  }
-}
 
 // ---------------------------------------------------------------------------
 // planned projection kernel: persistent CTAs over binned LORs, quad images
@@ -462,12 +317,6 @@ __global__ void __launch_bounds__(kMaxBlock) planned_kernel(const ProjParams p) 
 // a group step through consecutive planes (k = k0 + lane, k0 + lane + G, ...),
 // so their quad loads / reductions touch consecutive 16-byte entries.
 // ---------------------------------------------------------------------------
-template <int G>
-__device__ __forceinline__ float group_sum(float v) {
-#pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
 template <int MODE, bool BACK, bool LUT, int G>
 __global__ void __launch_bounds__(kMaxBlock) group_kernel(const ProjParams p) {
@@ -1401,8 +1250,24 @@ int planned(jp_plan pl, int mode, bool back, const float* in, float* out, int64_
   const bool lut = (mode != 0) && ((!(pl->opts.flags & JP_PLAN_TOF_EXACT) && !p.sig) || p.tof.user);
   const int block = pick_block(pl->opts.block, mode, p.tof, lut);
   cudaStream_t st = (cudaStream_t)stream;
-  const int64_t max_quad = std::max(std::max(p.ql.size[0], p.ql.size[1]), p.ql.size[2]);
   int lpw = pl->opts.lors_per_warp;
+  const bool sorted = !(pl->opts.flags & (JP_PLAN_KEEP_ORDER | JP_PLAN_INTERLEAVED));
+  if (sorted && mode != 1 && (pl->opts.flags & JP_PLAN_TILES) &&
+      (lpw == 0 || lpw == 1 || lpw == 2 || lpw == 4 || lpw == 8)) {
+    // shared-memory tiles over the plan's lines (frame, axis, slope, offset)
+    p.line_end = pl->hist;
+    p.lines_per_axis = pl->dims.slope_bins * pl->dims.offset_bins;
+    p.lines_per_frame = 3 * p.lines_per_axis;
+    p.keys_per_line = pl->dims.window_bins * pl->dims.zoff_bins;
+    p.n_lines = (int64_t)pl->n_frames * p.lines_per_frame;
+    for (int a = 0; a < 3; ++a) p.kb[a] = pl->kb[a];
+    p.tile_T = pl->opts.tile_lors;
+    p.line_batch = 4;
+    p.vec4_out = back && aligned(out, 16) && (p.shared || (img_stride % 4) == 0);
+    const int lanes = (lpw == 1) ? 32 : (lpw == 2) ? 16 : (lpw == 8) ? 4 : 8;
+    return launch_tile(p, mode, back, lut, lanes, std::min(pl->opts.block, kMaxBlock), st);
+  }
+  const int64_t max_quad = std::max(std::max(p.ql.size[0], p.ql.size[1]), p.ql.size[2]);
   if (lpw == 0) lpw = (!back || mode == 1) ? 32 : 4;
   if (mode == 1 && !back) lpw = 32;
   p.kfast = (lpw == 32) ? 0 : 1;

@@ -26,6 +26,7 @@ TOF_MODES = {"nontof": 0, "tof_sino": 1, "tof_lm": 2}
 JP_PLAN_KEEP_ORDER = 1
 JP_PLAN_TOF_EXACT = 2
 JP_PLAN_INTERLEAVED = 4
+JP_PLAN_TILES = 8
 OSEM_PATHS = {"auto": 0, "quads": 1, "direct": 2}
 OSEM_DIRECT_VOXELS_PER_EVENT = 24  # JP_OSEM_DIRECT_VOXELS_PER_EVENT
 
@@ -52,7 +53,7 @@ class ResolutionC(ctypes.Structure):
 class PlanOptsC(ctypes.Structure):
     _fields_ = [("block", I32), ("slope_bins", I32), ("offset_bins", I32), ("window_bins", I32),
                 ("tof_bin_width", F32), ("lors_per_warp", I32), ("flags", I32), ("zoff_bins", I32),
-                ("max_ctas_per_sm", I32)]
+                ("max_ctas_per_sm", I32), ("tile_lors", I32)]
 
 
 _lib = None
@@ -85,7 +86,7 @@ _SIGS = {
     "jp_osem_subset_tof_lm_dev": [P, I32, I32, P, P, F32, P, P, P],
     "jp_osem_subset_tof_lm_ex": [P, I32, I32, P, P, F32, F32, P, P, P, I32, P, P],
     "jp_gauss3d": [P, P, P, I32, P, P, P],
-    "jp_poisson_loglik_value": [P, P, P, P, I64, P, P],
+    "jp_poisson_loglik_value": [P, P, P, P, I64, P, P, P],
     "jp_poisson_loglik_grad": [P, P, P, P, P, I64, P, P],
     "jp_back_tof_lm_noalloc": [P, P, P, P, I64, P, P, P, P, P],
     "jp_bench_red": [P, I64, I32, I32, P, P],
@@ -232,11 +233,13 @@ class Plan:
 
 
 def _opts(block=0, slope_bins=0, offset_bins=0, window_bins=0, tof_bin_width=0.0, keep_order=False,
-          tof_exact=False, lors_per_warp=0, interleaved=False, zoff_bins=0, max_ctas_per_sm=0):
+          tof_exact=False, lors_per_warp=0, interleaved=False, zoff_bins=0, max_ctas_per_sm=0, tiles=False,
+          tile_lors=0):
     flags = ((JP_PLAN_KEEP_ORDER if keep_order else 0) | (JP_PLAN_TOF_EXACT if tof_exact else 0)
-             | (JP_PLAN_INTERLEAVED if interleaved else 0))
+             | (JP_PLAN_INTERLEAVED if interleaved else 0) | (JP_PLAN_TILES if tiles else 0))
     return PlanOptsC(int(block), int(slope_bins), int(offset_bins), int(window_bins),
-                     float(tof_bin_width), int(lors_per_warp), flags, int(zoff_bins), int(max_ctas_per_sm))
+                     float(tof_bin_width), int(lors_per_warp), flags, int(zoff_bins), int(max_ctas_per_sm),
+                     int(tile_lors))
 
 
 def jp_plan_create_batch(xs, xe, geom, frame_offsets, tof_bin=None, delta=None, stream=None,
@@ -560,21 +563,29 @@ def jp_gauss3d(img, geom, fwhm_mm, truncate: float = 4.0, out=None, work=None, s
     return out
 
 
-def jp_poisson_loglik_value(plan: Optional[Plan], proj, w, b, out=None, stream=None):
-    """sum_e w_e log(p_e + b_frame(e)) as a device double (0-dim tensor)."""
-    out = torch.empty((), dtype=torch.float64, device=proj.device) if out is None else out
+LOGLIK_BLOCKS = 1024  # JP_LOGLIK_BLOCKS
+
+
+def jp_poisson_loglik_value(plan: Optional[Plan], proj, w, b, out=None, work=None, stream=None):
+    """sum_e w_e log(p_e + b_frame(e)) as a device float (0-dim tensor),
+    an FP32 compensated sum; ``work`` is scratch of 2 * LOGLIK_BLOCKS floats."""
+    out = torch.empty((), dtype=torch.float32, device=proj.device) if out is None else out
+    work = torch.empty(2 * LOGLIK_BLOCKS, dtype=torch.float32, device=proj.device) if work is None else work
+    if work.numel() < 2 * LOGLIK_BLOCKS:
+        raise ValueError("work needs 2 * LOGLIK_BLOCKS floats")
     _check(load().jp_poisson_loglik_value(plan.handle if plan is not None else None, _ptr(proj, torch.float32, "proj"),
                                           _ptr(w, torch.float32, "w"), _ptr(b, torch.float32, "b"), int(proj.numel()),
-                                          _ptr(out, torch.float64, "value"), _stream(stream)))
+                                          _ptr(out, torch.float32, "value"), _ptr(work, torch.float32, "work"),
+                                          _stream(stream)))
     return out
 
 
 def jp_poisson_loglik_grad(plan: Optional[Plan], proj, w, b, scale=None, out=None, stream=None):
-    """grad_e = scale * w_e / (p_e + b_frame(e)) (scale: device double or None)."""
+    """grad_e = scale * w_e / (p_e + b_frame(e)) (scale: device float or None)."""
     out = torch.empty_like(proj) if out is None else out
     _check(load().jp_poisson_loglik_grad(plan.handle if plan is not None else None, _ptr(proj, torch.float32, "proj"),
                                          _ptr(w, torch.float32, "w"), _ptr(b, torch.float32, "b"),
-                                         _ptr(scale, torch.float64, "scale"), int(proj.numel()),
+                                         _ptr(scale, torch.float32, "scale"), int(proj.numel()),
                                          _ptr(out, torch.float32, "grad"), _stream(stream)))
     return out
 
