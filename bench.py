@@ -33,20 +33,12 @@ EVENTS_PER_FRAME = 40_000_000
 METRIC = "TOF listmode fwd+back events/s"
 UNIT = "events/s"
 
-# From an ncu capture of the (unchanged) back-projection kernel on one frame
-# of 10M events: L2 reduction sectors per plane sample
-# (l1tex__t_sectors_pipe_lsu_mem_global_op_red / samples) and DRAM bytes per
-# event (dram__bytes_read.sum + dram__bytes_write.sum over events), scaled to
-# a full launch by the events it processes.
-BACK_SECTORS_PER_SAMPLE = 534_830_072 / 732_745_430
+# DRAM traffic of the TOF-listmode back projection per event (ncu
+# dram__bytes_read.sum + dram__bytes_write.sum of the quad-image group back
+# kernel on one 10M-event frame, 200x200x71), scaled to a launch by its
+# events: the traffic grows with the events; the per-frame image terms are
+# small.
 BACK_DRAM_BYTES_PER_EVENT = (608_469_248 + 76_418_304) / 10_000_000
-# non-TOF sinogram back projection (group kernel, plane-fastest quads):
-# l1tex reduction sectors / plane samples on the 266k-LOR small sinogram
-SINO_BACK_SECTORS_PER_SAMPLE = 6_298_790 / 8_856_832
-# TOF sinogram kernels (planned, bin-aligned weight table): warp instructions
-# per plane sample, ncu smsp__inst_executed / plane samples on a
-# 2,028,240-LOR view subset of the clinical TOF sinogram
-TOF_SINO_WARP_INSTR_PER_SAMPLE = {"fwd": 1_212_321_753 / 266_701_248, "back": 1_592_531_301 / 266_701_248}
 
 
 # ---------------------------------------------------------------------------
@@ -299,8 +291,10 @@ def run_ours(args):
         ms = float(tt.item())
     kern = {k: statistics.mean(s.elapsed_time(e) for s, e in v) for k, v in timers.items() if v}
 
-    # exact algorithmic work of one TOF-LM launch
-    samples = ops.jp_count_samples(plan, "nontof" if nontof else "tof_lm", tof)
+    # exact algorithmic work of one launch, counted on the device
+    mode = "nontof" if nontof else "tof_lm"
+    samples = ops.jp_count_samples(plan, mode, tof)
+    requests = ops.jp_count_red_requests(plan, mode, tof)
     value = n_total * ws / (ms / 1e3)
 
     # ---- e2e through the public API with host buffers --------------------
@@ -316,6 +310,11 @@ def run_ours(args):
     del W["xs"], W["xe"], W["ds"], W["de"], W["w"], W["bvec"]
     W["tb"] = None
     torch.cuda.empty_cache()
+    workloads = None
+    if not args.no_extra and rank == 0 and ws == 1 and not nontof:
+        # the other workloads at one GPU: configs 2 and 3 and the paper's 34-subset iteration
+        workloads = {name: measure_sino(name, 5, 3) for name in ("sino_clinical", "tof_sino")}
+        workloads["lm_osem_iter"] = measure_lm_osem_iter(5, 3, args.fwhm)
     serving = None
     if not args.no_serving and rank == 0 and not nontof:
         rates = [float(r) for r in args.serving_rates.split(",")]
@@ -324,15 +323,16 @@ def run_ours(args):
 
     if rank == 0:
         peaks, peak_kind = measured_peaks()
-        # dominant kernel: the back projection (scatter), reported against HBM
-        dom = "back" if kern.get("back", 0) >= kern.get("fwd", 0) else "fwd"
         nvox = int(np.prod(g.shape))
-        alg_bytes = n_total * (24 + (0 if nontof else 2) + 4) + n_frames * nvox * 4 * (2 if dom == "back" else 1)
-        achieved = alg_bytes / (kern[dom] / 1e3) / 1e9
-        # binding resource: L2 reduction sectors of the back projection vs the measured ceiling
-        red_rate = samples / (kern["back"] / 1e3)
-        sec_rate = red_rate * BACK_SECTORS_PER_SAMPLE
+        # HBM view of the back projection (30 B per event + the images)
+        alg_bytes = n_total * (24 + (0 if nontof else 2) + 4) + n_frames * nvox * 4 * 2
+        achieved = alg_bytes / (kern["back"] / 1e3) / 1e9
+        # binding resource: the back projection's L2 reduction requests (counted
+        # on the device for this launch) against the reduction ceiling
+        # measured in this run
+        sec_rate = requests / (kern["back"] / 1e3)
         sec_peak = max(r["sectors_per_s"] for r in red.values())
+        kname = "back_nontof_lm" if nontof else "back_tof_lm"
         line = {
             "metric": METRIC if not nontof else "non-TOF listmode fwd+back events/s",
             "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -349,21 +349,21 @@ def run_ours(args):
             "kernel_ms": kern,
             "samples_per_step": samples,
             "events_per_s_excl_binning": n_total * ws / ((ms - kern.get("bin", 0.0)) / 1e3),
-            "roofline": {"bound": "hbm", "kernel": f"{dom}_{'nontof' if nontof else 'tof'}_lm", "achieved": achieved,
-                         "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                         "traffic": (BACK_DRAM_BYTES_PER_EVENT * n_total if dom == "back" and not nontof
-                                     else None),
-                         "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes},
-            "binding_roofline": {"kernel": "back_nontof_lm" if nontof else "back_tof_lm",
-                                 "resource": "L2 reduction sectors (16-byte RED per sample)",
-                                 "achieved": sec_rate, "peak": sec_peak, "unit": "sectors/s",
-                                 "frac": sec_rate / sec_peak, "reductions_per_s": red_rate,
-                                 "sectors_per_reduction": BACK_SECTORS_PER_SAMPLE,
-                                 "peak_patterns": {str(k): v["sectors_per_s"] for k, v in red.items()},
-                                 "peak_source": "jp_bench_red_pattern (measured in this run), max over patterns"},
+            "roofline": {"bound": "l2", "kernel": kname,
+                         "resource": "L2 reduction requests (32-byte sector operations of the 16-byte "
+                                     "vector reductions, one per plane sample)",
+                         "achieved": sec_rate, "peak": sec_peak, "unit": "sectors/s", "frac": sec_rate / sec_peak,
+                         "traffic": (BACK_DRAM_BYTES_PER_EVENT * n_total if not nontof else None),
+                         "requests_per_launch": requests, "requests_per_sample": requests / max(samples, 1),
+                         "peak_patterns": {str(k): v["sectors_per_s"] for k, v in red.items()},
+                         "peak_source": "jp_bench_red_pattern (measured in this run), max over patterns"},
+            "hbm_roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved,
+                             "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                             "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes},
             "clocks": clk,
             "gpu_launches": int(launches),
             "e2e": e2e,
+            "workloads": workloads,
             "serving": serving,
         }
         if cpu_sample is not None:
@@ -464,34 +464,18 @@ SINO_WORKLOADS = {
 }
 
 
-def issue_roofline(dom, samples, kernel_ms, clk, dev):
-    """TOF sinogram kernels are bound by instruction issue (about 7 TOF bins
-    per plane sample, each a table read, an interpolation and an
-    accumulation): achieved warp instructions/s against 4 schedulers per SM
-    issuing one warp instruction per cycle each at the sampled SM clock."""
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
-    peak = sms * 4 * float(mhz) * 1e6
-    wi = TOF_SINO_WARP_INSTR_PER_SAMPLE[dom]
-    achieved = samples * wi / (kernel_ms / 1e3)
-    return {"kernel": f"{dom}_tof_sino", "resource": "instruction issue", "bound": "alu",
-            "achieved": achieved, "peak": peak, "unit": "warp instructions/s", "frac": achieved / peak,
-            "warp_instructions_per_sample": wi, "clock_mhz": float(mhz),
-            "instructions_source": "ncu smsp__inst_executed / plane samples, 2.03M-LOR view subset"}
-
-
-def run_sino(args):
+def measure_sino(workload, steps, warmup, opts=None, cpu_lors=0):
     """One step = forward + back projection of every LOR of the sinogram
     (LOR endpoints and their plan are computed once, outside the timed
-    region, as the paper excludes LOR set-up).  value = LORs projected
-    forward and back per second."""
-    from paper_2212_12519_gb300 import build as jbuild, ops, synth
-    ws, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    jbuild.build()
-    ops.load()
-    spec_n, geom_n, ph_n, sb, is_tof = SINO_WORKLOADS[args.workload]
+    region, as the paper excludes LOR set-up).  Returns the bench line:
+    LORs projected forward and back per second, per-kernel CUDA-event times,
+    and the binding roofline of each kernel from work counted on the device
+    against a ceiling measured in the same run (non-TOF: L2 reduction
+    requests of the back projection vs the reduction ceiling; TOF: bin
+    evaluations vs the per-bin operation's ceiling)."""
+    from paper_2212_12519_gb300 import ops, synth
+    dev = torch.device("cuda")
+    spec_n, geom_n, ph_n, sb, is_tof = SINO_WORKLOADS[workload]
     spec, g, phs = getattr(synth, spec_n), getattr(synth, geom_n), getattr(synth, ph_n)
     tof = synth.TOF_CLINICAL if is_tof else None
     img = synth.ellipsoid_phantom(g, phs, sb + 1, device=dev)
@@ -503,7 +487,7 @@ def run_sino(args):
         y = torch.poisson(torch.full((n, tof.n_bins), 2.0, device=dev), generator=gen)
     else:
         y = torch.rand(n, generator=gen, device=dev)
-    plan = ops.jp_plan_create(xs, xe, g, **plan_opts(args))
+    plan = ops.jp_plan_create(xs, xe, g, **(opts or {}))
     out = torch.zeros(g.shape, device=dev)
     stream = torch.cuda.current_stream()
     tim = {"fwd": [], "back": []}
@@ -516,70 +500,77 @@ def run_sino(args):
         b.record(stream)
         tim[name].append((a, b))
 
-    def step(record=True):
-        f = (lambda: ops.jp_fwd_tof_sino(plan, img, tof)) if is_tof else (lambda: ops.jp_fwd(plan, img))
-        bk = (lambda: ops.jp_back_tof_sino(plan, y, tof, out)) if is_tof else (lambda: ops.jp_back(plan, y, out))
-        if record:
-            rec("fwd", f)
-            rec("back", bk)
-        else:
-            f()
-            bk()
-
-    for _ in range(args.warmup):
-        step(False)
+    f = (lambda: ops.jp_fwd_tof_sino(plan, img, tof)) if is_tof else (lambda: ops.jp_fwd(plan, img))
+    bk = (lambda: ops.jp_back_tof_sino(plan, y, tof, out)) if is_tof else (lambda: ops.jp_back(plan, y, out))
+    for _ in range(warmup):
+        f()
+        bk()
     torch.cuda.synchronize()
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     launches0 = ops.jp_launch_count()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     rng_id = torch.cuda.nvtx.range_start("timed")
     t0.record(stream)
-    for _ in range(args.steps):
-        step()
+    for _ in range(steps):
+        rec("fwd", f)
+        rec("back", bk)
     t1.record(stream)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_end(rng_id)
     launches = ops.jp_launch_count() - launches0
     clk = clocks.stop()
-    ms = t0.elapsed_time(t1) / args.steps
+    ms = t0.elapsed_time(t1) / steps
     kern = {k: statistics.mean(a.elapsed_time(b) for a, b in v) for k, v in tim.items()}
     samples = ops.jp_count_samples(plan, "nontof")
-    red = {pt: ops.jp_bench_red(pattern=pt) for pt in (0, 1, 2)}
-    sec_peak = max(r["sectors_per_s"] for r in red.values())
     peaks, peak_kind = measured_peaks()
     nb = tof.n_bins if is_tof else 1
     dom = "back" if kern["back"] >= kern["fwd"] else "fwd"
     nvox = int(np.prod(g.shape))
     alg = n * (24 + 4 * nb) + nvox * 4 * (2 if dom == "back" else 1)
-    achieved = alg / (kern[dom] / 1e3) / 1e9
+    hbm = alg / (kern[dom] / 1e3) / 1e9
+    hbm_line = {"bound": "hbm", "kernel": f"{dom}_{workload}", "achieved": hbm, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": hbm / peaks["hbm_gbs"], "traffic": None, "peak_source": peak_kind,
+                "alg_bytes_per_launch": alg}
+    if is_tof:
+        bins = ops.jp_count_samples(plan, "tof_sino", tof)
+        binding = {}
+        for dname, direction in (("fwd", 0), ("back", 1)):
+            ceil = ops.jp_bench_tof_bins(tof, direction)["bins_per_s"]
+            ach = bins / (kern[dname] / 1e3)
+            binding[dname] = {"kernel": f"{dname}_tof_sino", "resource": "TOF bin evaluations (table read, "
+                              "interpolation and accumulation per bin)", "bound": "alu", "achieved": ach,
+                              "peak": ceil, "unit": "bins/s", "frac": ach / ceil, "bins_per_launch": bins,
+                              "bins_per_sample": bins / max(samples, 1),
+                              "peak_source": "jp_bench_tof_bins (measured in this run)"}
+        roofline = dict(binding["back"])
+    else:
+        req = ops.jp_count_red_requests(plan, "nontof")
+        red = {pt: ops.jp_bench_red(pattern=pt) for pt in (0, 1, 2)}
+        peak = max(r["sectors_per_s"] for r in red.values())
+        ach = req / (kern["back"] / 1e3)
+        roofline = {"bound": "l2", "kernel": f"back_{workload}",
+                    "resource": "L2 reduction requests (32-byte sector operations)", "achieved": ach,
+                    "peak": peak, "unit": "sectors/s", "frac": ach / peak, "traffic": None,
+                    "requests_per_launch": req, "requests_per_sample": req / max(samples, 1),
+                    "peak_source": "jp_bench_red_pattern (measured in this run), max over patterns"}
+        binding = None
     line = {"metric": "LOR projections (fwd+back)/s", "value": n / (ms / 1e3), "unit": "LOR/s",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "n_gpus": 1, "steps": steps, "warmup": warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": args.workload, "lors": n, "image": list(g.shape), "tof_bins": nb,
+            "config": {"workload": workload, "lors": n, "image": list(g.shape), "tof_bins": nb,
                        "l2": "LOR arrays larger than L2" if n * 24 > 200e6 else "small case, L2-resident"},
-            "kernel_ms": kern, "samples_per_step": samples,
-            "roofline": {"bound": "hbm", "kernel": f"{dom}_{args.workload}", "achieved": achieved,
-                         "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                         "traffic": None, "peak_source": peak_kind, "alg_bytes_per_launch": alg},
-            "binding_roofline": (
-                {"kernel": f"back_{args.workload}",
-                 "resource": "L2 reduction sectors (16-byte RED per sample)",
-                 "achieved": samples / (kern["back"] / 1e3) * SINO_BACK_SECTORS_PER_SAMPLE, "peak": sec_peak,
-                 "unit": "sectors/s",
-                 "frac": samples / (kern["back"] / 1e3) * SINO_BACK_SECTORS_PER_SAMPLE / sec_peak,
-                 "reductions_per_s": samples / (kern["back"] / 1e3),
-                 "sectors_per_reduction": SINO_BACK_SECTORS_PER_SAMPLE,
-                 "sectors_source": "ncu l1tex red sectors / plane samples, 266k-LOR small sinogram"}
-                if not is_tof else issue_roofline(dom, samples, kern[dom], clk, dev)),
+            "kernel_ms": kern, "samples_per_step": samples, "roofline": roofline, "hbm_roofline": hbm_line,
             "clocks": clk, "gpu_launches": int(launches)}
-    if not args.no_cpu_baseline:
+    if binding is not None:
+        line["binding_roofline"] = binding
+    if cpu_lors:
         import oracle
         oracle.build()
         threads = os.cpu_count() or 1
-        m = min(n, args.cpu_lors)
+        m = min(n, cpu_lors)
         sx, se = xs[:m].cpu().numpy(), xe[:m].cpu().numpy()
         yy = y[:m].cpu().numpy()
         im = img.cpu().numpy()
@@ -590,8 +581,20 @@ def run_sino(args):
         dt = time.perf_counter() - t
         line["cpu_baseline"] = {"value": m / dt, "unit": "LOR/s", "cores": threads, "kind": "oracle",
                                 "sample": f"first {m} of {n} LORs, FP64 fwd+back, {dt:.1f} s"}
-    print(json.dumps(line), flush=True)
     plan.destroy()
+    del xs, xe, y, out, img
+    torch.cuda.empty_cache()
+    return line
+
+
+def run_sino(args):
+    from paper_2212_12519_gb300 import build as jbuild, ops
+    torch.cuda.set_device(dist_env()[2])
+    jbuild.build()
+    ops.load()
+    line = measure_sino(args.workload, args.steps, args.warmup, plan_opts(args),
+                        0 if args.no_cpu_baseline else args.cpu_lors)
+    print(json.dumps(line), flush=True)
 
 
 # ---------------------------------------------------------------------------
@@ -648,25 +651,24 @@ def run_sino_osem(args):
     so.close()
 
 
-def run_lm_osem_iter(args):
-    """The paper's LM-OSEM timing (Sec. 3, discussed in Sec. 4): one TOF listmode OSEM iteration
-    (34 subset updates, each with the two resolution-model convolutions)
-    for one frame of 40e6 and of 1.25e6 events on the 200x200x71 grid.
-    The frame's subset plan (binning) is built once before its iterations
-    and timed separately; one iteration is a replayed CUDA graph."""
-    from paper_2212_12519_gb300 import build as jbuild, ops, osem, synth
-    jbuild.build()
-    ops.load()
+def measure_lm_osem_iter(steps, warmup, fwhm):
+    """The paper's LM-OSEM timing (Sec. 3, discussed in Sec. 4): one TOF
+    listmode OSEM iteration (34 subset updates, each with the two
+    resolution-model convolutions when fwhm > 0) for one frame of 40e6 and
+    of 1.25e6 events on the 200x200x71 grid.  The frame's subset plan
+    (binning) is built once before its iterations and timed separately; one
+    iteration is a replayed CUDA graph."""
+    from paper_2212_12519_gb300 import osem, synth
     dev = torch.device("cuda")
     g, tof = synth.GEOM_CLINICAL, synth.TOF_CLINICAL
     s_raw, _ = osem.sensitivity(g, check=False)
-    sens = osem.resolution_sensitivity(s_raw, g, args.fwhm)
+    sens = osem.resolution_sensitivity(s_raw, g, fwhm)
     ph = synth.ellipsoid_phantom(g, synth.PHANTOM_CLINICAL, 9201, device=dev)
     b = synth.background_level(ph, tof)
     out = []
     for n_ev in (40_000_000, 1_250_000):
         xs, xe, tb = synth.lm_events(ph, g, synth.SCANNER_CLINICAL, tof, n_ev, seed=9202, device=dev)
-        spec = osem.FrameSpec(xs, xe, tb, g, b, n_iter=1, n_sub=34, fwhm_mm=args.fwhm)
+        spec = osem.FrameSpec(xs, xe, tb, g, b, n_iter=1, n_sub=34, fwhm_mm=fwhm)
         a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         a.record()
@@ -675,25 +677,34 @@ def run_lm_osem_iter(args):
         torch.cuda.synchronize()
         bin_ms = a.elapsed_time(e)
         fr.run_graph()  # capture + one iteration
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             fr.run_graph()
         torch.cuda.synchronize()
         a.record(fr.stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             fr.run_graph()
         e.record(fr.stream)
         torch.cuda.synchronize()
-        it_ms = a.elapsed_time(e) / args.steps
+        it_ms = a.elapsed_time(e) / steps
         out.append({"events": n_ev, "subsets": 34, "iteration_ms": it_ms, "plan_ms": bin_ms,
-                    "convolutions_per_iteration": 68 if args.fwhm > 0 else 0,
+                    "convolutions_per_iteration": 68 if fwhm > 0 else 0,
                     "paper_gpu_iteration_ms": 600.0 if n_ev == 40_000_000 else 57.0})
         fr.release()
         del fr, xs, xe, tb, spec
         torch.cuda.empty_cache()
-    print(json.dumps({"metric": "TOF LM-OSEM ms per iteration (34 subsets)",
-                      "config": {"workload": "lm_osem_iteration_200x200x71", "resolution_fwhm_mm": args.fwhm,
-                                 "steps": args.steps, "warmup": args.warmup},
-                      "rows": out}), flush=True)
+    del sens, s_raw, ph
+    torch.cuda.empty_cache()
+    return {"metric": "TOF LM-OSEM ms per iteration (34 subsets)",
+            "config": {"workload": "lm_osem_iteration_200x200x71", "resolution_fwhm_mm": fwhm,
+                       "steps": steps, "warmup": warmup},
+            "rows": out}
+
+
+def run_lm_osem_iter(args):
+    from paper_2212_12519_gb300 import build as jbuild, ops
+    jbuild.build()
+    ops.load()
+    print(json.dumps(measure_lm_osem_iter(args.steps, args.warmup, args.fwhm)), flush=True)
 
 
 def run_layout_study(args):
@@ -811,34 +822,67 @@ def run_profile_tof_sino(args):
 
 
 def run_profile_case(args):
-    """One frame of --events TOF listmode events (200x200x71): the plan
-    (key, scan x3, scatter, flags), then three times forward + back
-    projection (each timed with CUDA events), then a rebind."""
+    """One frame of --events listmode events (200x200x71, TOF unless
+    --lm-mode nontof): the plan (key, scan x3, scatter, flags), then three
+    times forward + back projection (each timed with CUDA events), then a
+    rebind."""
     from paper_2212_12519_gb300 import build as jbuild, ops, synth
     jbuild.build()
     ops.load()
     dev = torch.device("cuda")
     g, tof = synth.GEOM_CLINICAL, synth.TOF_CLINICAL
+    nontof = args.lm_mode == "nontof"
     ph = synth.ellipsoid_phantom(g, synth.PHANTOM_CLINICAL, 4001, device=dev)
     xs, xe, tb = synth.lm_events(ph, g, synth.SCANNER_CLINICAL, tof, args.events, seed=4051, device=dev)
     y = torch.rand(args.events, device=dev)
     img = torch.zeros(g.shape, device=dev)
     popts = plan_opts(args)
-    plan = ops.jp_plan_create(xs, xe, g, tof_bin=tb, tof_bin_width=tof.bin_width, **popts)
+    if nontof:
+        plan = ops.jp_plan_create(xs, xe, g, **popts)
+        fwd, back = (lambda: ops.jp_fwd(plan, ph)), (lambda: ops.jp_back(plan, y, img))
+    else:
+        plan = ops.jp_plan_create(xs, xe, g, tof_bin=tb, tof_bin_width=tof.bin_width, **popts)
+        fwd, back = (lambda: ops.jp_fwd_tof_lm(plan, ph, tof)), (lambda: ops.jp_back_tof_lm(plan, y, tof, img))
     ms = {"fwd": [], "back": []}
     for _ in range(3):
-        for name, fn in (("fwd", lambda: ops.jp_fwd_tof_lm(plan, ph, tof)),
-                         ("back", lambda: ops.jp_back_tof_lm(plan, y, tof, img))):
+        for name, fn in (("fwd", fwd), ("back", back)):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
             fn()
             b.record()
             ms[name].append((a, b))
-    ops.jp_plan_rebind(plan, xs, xe, tof_bin=tb)
+    ops.jp_plan_rebind(plan, xs, xe, tof_bin=None if nontof else tb)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_case": "tof_lm", "events": args.events, "path": args.path, "plan_opts": popts,
+    mode = "nontof" if nontof else "tof_lm"
+    print(json.dumps({"profile_case": mode, "events": args.events, "path": args.path, "plan_opts": popts,
                       "ms": {k: [a.elapsed_time(b) for a, b in v] for k, v in ms.items()},
-                      "samples": ops.jp_count_samples(plan, "tof_lm", tof)}))
+                      "samples": ops.jp_count_samples(plan, mode, tof)}))
+    plan.destroy()
+
+
+def run_profile_sino(args):
+    """One view subset (1 of 34, 10 views) of the clinical non-TOF sinogram:
+    4,056,480 LORs (their endpoints and plan records exceed L2), forward and
+    back projection three times, for ncu captures of the non-TOF sinogram
+    kernels."""
+    from paper_2212_12519_gb300 import build as jbuild, ops, synth
+    jbuild.build()
+    ops.load()
+    dev = torch.device("cuda")
+    g = synth.GEOM_CLINICAL
+    img = synth.ellipsoid_phantom(g, synth.PHANTOM_CLINICAL, 2001, device=dev)
+    xs, xe = synth.sinogram_lors(synth.SINO_CLINICAL.subset(0, 34), device=dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(2002)
+    y = torch.rand(xs.shape[0], generator=gen, device=dev)
+    plan = ops.jp_plan_create(xs, xe, g, **plan_opts(args))
+    out = torch.zeros(g.shape, device=dev)
+    for _ in range(3):
+        ops.jp_fwd(plan, img)
+        ops.jp_back(plan, y, out)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_sino": int(xs.shape[0]), "samples": ops.jp_count_samples(plan, "nontof"),
+                      "red_requests": ops.jp_count_red_requests(plan, "nontof")}))
     plan.destroy()
 
 
@@ -879,42 +923,77 @@ def time_gauss3d(g, fwhm_mm, reps=200):
 
 
 def run_serving(n_requests=200, rates=(1.0,), pool_events=20_000_000, max_slots=4, budget_gb=None,
-                use_graphs=True, seed=5001, fwhm_mm=4.5):
-    from paper_2212_12519_gb300 import osem, serve, synth
+                use_graphs=True, seed=5001, fwhm_mm=4.5, extra_arms=True, control_rates=(1.0, 1.5, 3.0)):
+    """Served listmode OSEM (config 5): the batched server (binned plans,
+    graph-replayed iterations, continuous batching over max_slots
+    concurrent frames) against sequential plain per-frame projection, at
+    arrival rates given as multiples of the sequential capacity mu_seq.
+    With extra_arms: the batched server with one slot (binned kernels and
+    graphs, no overlap of frames), its capacity and at control_rates (the
+    last close to the batched capacity, where the sequential server is long
+    saturated and is not run), which separates what continuous batching
+    buys from what the binned kernels buy; and, when fwhm_mm > 0, the same
+    comparison without the resolution model."""
+    from paper_2212_12519_gb300 import serve, synth
     tof = synth.TOF_CLINICAL
     t0 = time.perf_counter()
     pools = serve.make_event_pools(tof, pool_events=pool_events)
-    sens, checks = {}, {}
-    for shape, pool in pools.items():
-        s, checks[str(shape)] = osem.sensitivity(pool["geom"])
-        sens[shape] = osem.resolution_sensitivity(s, pool["geom"], fwhm_mm)
-    setup_s = time.perf_counter() - t0
     geoms = [p["geom"] for p in pools.values()]
-    res_model = time_gauss3d(synth.GEOM_CLINICAL, fwhm_mm) if fwhm_mm > 0 else None
-    # mu_seq: sequential plain server, all requests available at once
-    reqs = serve.make_requests(pools, n_requests, rate=1e9, seed=seed, fwhm_mm=fwhm_mm)
-    seq = serve.OSEMServer(sens, tof, mode="sequential")
-    base = seq.run(reqs)
-    mu = base["frames_per_s"]
-    bat = serve.OSEMServer(sens, tof, mode="batched", max_slots=max_slots, use_graphs=use_graphs,
-                           hbm_budget=None if budget_gb is None else int(budget_gb * 2 ** 30))
-    bat.reserve(int(2e7), geoms, fwhm_mm=fwhm_mm)
-    serve.reset(reqs)
-    cap = bat.run(reqs)
-    out = {"requests": n_requests, "mu_seq_frames_per_s": mu, "batched_capacity_frames_per_s": cap["frames_per_s"],
-           "sensitivity_fp64_check": checks, "setup_s": setup_s, "resolution_fwhm_mm": fwhm_mm,
-           "resolution_model": res_model, "sweep": []}
-    for f in rates:
-        lam = f * mu
-        reqs = serve.make_requests(pools, n_requests, rate=lam, seed=seed, fwhm_mm=fwhm_mm)
-        r_seq = seq.run(reqs)
+    budget = None if budget_gb is None else int(budget_gb * 2 ** 30)
+
+    def arm(fwhm, arm_rates, one_slot_rates):
+        from paper_2212_12519_gb300 import osem
+        sens, checks = {}, {}
+        for shape, pool in pools.items():
+            s_, checks[str(shape)] = osem.sensitivity(pool["geom"])
+            sens[shape] = osem.resolution_sensitivity(s_, pool["geom"], fwhm)
+        res_model = time_gauss3d(synth.GEOM_CLINICAL, fwhm) if fwhm > 0 else None
+        # mu_seq: sequential plain server, all requests available at once
+        reqs = serve.make_requests(pools, n_requests, rate=1e9, seed=seed, fwhm_mm=fwhm)
+        seq = serve.OSEMServer(sens, tof, mode="sequential")
+        mu = seq.run(reqs)["frames_per_s"]
+        bat = serve.OSEMServer(sens, tof, mode="batched", max_slots=max_slots, use_graphs=use_graphs,
+                               hbm_budget=budget)
+        bat.reserve(int(2e7), geoms, fwhm_mm=fwhm)
+        one = None
+        if one_slot_rates:
+            one = serve.OSEMServer(sens, tof, mode="batched", max_slots=1, use_graphs=use_graphs)
+            one.reserve(int(2e7), geoms, fwhm_mm=fwhm)
         serve.reset(reqs)
-        r_bat = bat.run(reqs)
-        out["sweep"].append({"rate_x_mu_seq": f, "rate_frames_per_s": lam,
-                             "sequential": {k: r_seq[k] for k in ("frames_per_s", "p50_ms", "p99_ms")},
-                             "batched": {k: r_bat[k] for k in ("frames_per_s", "p50_ms", "p99_ms", "events_per_s")}})
-    bat.close()
-    return out
+        cap = bat.run(reqs)
+        out = {"requests": n_requests, "mu_seq_frames_per_s": mu, "batched_capacity_frames_per_s": cap["frames_per_s"],
+               "sensitivity_fp64_check": checks, "resolution_fwhm_mm": fwhm, "resolution_model": res_model,
+               "max_slots": max_slots, "sweep": []}
+        if one is not None:
+            serve.reset(reqs)
+            out["batched_one_slot_capacity_frames_per_s"] = one.run(reqs)["frames_per_s"]
+        for f in sorted(set(arm_rates) | set(one_slot_rates or ())):
+            lam = f * mu
+            reqs = serve.make_requests(pools, n_requests, rate=lam, seed=seed, fwhm_mm=fwhm)
+            row = {"rate_x_mu_seq": f, "rate_frames_per_s": lam}
+            if f in arm_rates:
+                r_seq = seq.run(reqs)
+                row["sequential"] = {k: r_seq[k] for k in ("frames_per_s", "p50_ms", "p99_ms")}
+            serve.reset(reqs)
+            r_bat = bat.run(reqs)
+            row["batched"] = {k: r_bat[k] for k in ("frames_per_s", "p50_ms", "p99_ms", "events_per_s")}
+            if one is not None and f in one_slot_rates:
+                serve.reset(reqs)
+                r_one = one.run(reqs)
+                row["batched_one_slot"] = {k: r_one[k] for k in ("frames_per_s", "p50_ms", "p99_ms")}
+            out["sweep"].append(row)
+        bat.close()
+        if one is not None:
+            one.close()
+        del sens
+        torch.cuda.empty_cache()
+        return out
+
+    main = arm(fwhm_mm, list(rates), list(control_rates) if extra_arms else [])
+    if extra_arms and fwhm_mm > 0:
+        main["no_resolution_model"] = arm(0.0, [r for r in control_rates if r <= 1.5], list(control_rates))
+    main["setup_s"] = time.perf_counter() - t0
+    return main
 
 
 # ---------------------------------------------------------------------------
@@ -1017,11 +1096,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=200)
-    ap.add_argument("--serving-rates", default="0.5,0.8,1.0,1.5")
+    ap.add_argument("--serving-rates", default="0.8,1.0,1.5")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the clinical-sinogram, TOF-sinogram and LM-OSEM-iteration lines of the default run")
     ap.add_argument("--workload", default="tof_lm",
                     choices=["tof_lm", "nontof_lm", "sino_small", "sino_clinical", "tof_sino", "osem",
                              "sino_osem", "layout_study", "lm_osem_iter", "profile_case", "profile_osem",
-                             "profile_tof_sino"])
+                             "profile_tof_sino", "profile_sino"])
     ap.add_argument("--cpu-lors", type=int, default=200_000)
     ap.add_argument("--budget-gb", type=float, default=None)
     ap.add_argument("--no-graphs", action="store_true")
@@ -1034,6 +1115,8 @@ def main():
     ap.add_argument("--block", type=int, default=0, help="plan option: threads per CTA (0 = default)")
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="plan option: resident CTAs per SM (0 = default)")
     ap.add_argument("--lors-per-warp", type=int, default=0, help="plan option: LORs per warp (0 = default)")
+    ap.add_argument("--lm-mode", default="tof_lm", choices=["tof_lm", "nontof"],
+                    help="profile_case: TOF or non-TOF listmode")
     ap.add_argument("--event-sigma", action="store_true",
                     help="listmode workload with per-event TOF sigma (three timing classes)")
     args = ap.parse_args()
@@ -1045,6 +1128,8 @@ def main():
         run_profile_osem(args)
     elif args.workload == "profile_tof_sino":
         run_profile_tof_sino(args)
+    elif args.workload == "profile_sino":
+        run_profile_sino(args)
     elif args.workload in SINO_WORKLOADS:
         run_sino(args)
     elif args.workload == "sino_osem":

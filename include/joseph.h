@@ -439,34 +439,64 @@ int jp_osem_init(float* x, const float* sens, int64_t nvox, void* stream);
  * for the sensitivity-normalisation check sum_j (A^T 1)_j = sum_i (A 1)_i. */
 int jp_sum_f64(const float* x, int64_t n, double* out, void* stream);
 
-/* Number of plane samples the projector visits for the plan's LORs in the
- * given mode (0 non-TOF, 2 TOF listmode; TOF sinograms visit the non-TOF
- * planes), summed into *out (device uint64, overwritten).  Used to state
- * the algorithmic work of a launch (samples x bytes or flops per sample). */
+/* Algorithmic work of the plan's LORs, summed into *out (device uint64,
+ * overwritten): tof_mode 0 / 2, the plane samples the projector visits
+ * (non-TOF / TOF listmode, whose samples are the planes of the TOF window);
+ * tof_mode 1, the TOF bin evaluations of a TOF sinogram (over every plane
+ * sample, the bins whose window holds it: the per-bin work of the sinogram
+ * kernels).  Used to state the work of a launch (samples x bytes per sample,
+ * bins x operations per bin). */
 int jp_count_samples(jp_plan p, int32_t tof_mode, const jp_tof* t, uint64_t* out, void* stream);
+
+/* Throughput ceiling of the TOF-sinogram kernels' per-bin work (measurement
+ * helper): synthetic sample positions, each window's bins through the
+ * bin-aligned shared-memory table of t (Gaussian kernels only) and
+ * accumulated into per-thread shared-memory bins (direction 0, the
+ * forward's operation) or dotted with per-thread shared-memory values
+ * (direction 1, the back projection's), per_thread samples per thread on
+ * every resident thread of the GPU.  *ms_out (host) is the time of one
+ * timed launch after a warm-up one, *bins_out (device uint64) the bins it
+ * evaluated.  Synchronises the stream.  Errors: JP_ERR_ARG, JP_ERR_ALIGN,
+ * JP_ERR_CUDA. */
+int jp_bench_tof_bins(const jp_tof* t, int32_t direction, int32_t per_thread, float* ms_out, uint64_t* bins_out,
+                      void* stream);
+
+/* Number of L2 reduction requests (32-byte sector operations) the plan's
+ * quad-image back projection issues in the given mode (0 non-TOF, 2 TOF
+ * listmode), counted on the device by replaying that kernel's schedule:
+ * its warp chunks, its lane -> (LOR, plane) map and its quad entries, with
+ * every LOR's input nonzero.  A warp instruction's 16-byte reductions
+ * coalesce into one request per 32-byte sector and lane slot; a sector
+ * holds two quad entries, so it costs the larger of their lane counts.
+ * Frames are taken with their own image slots.  *out (device uint64) is
+ * overwritten.  This is the work unit of the back projection's binding
+ * roofline (the L2 reduction throughput).  Errors: JP_ERR_ARG, JP_ERR_ALIGN,
+ * JP_ERR_STATE (tile, interleaved or one-LOR-per-thread plans), JP_ERR_CUDA. */
+int jp_count_red_requests(jp_plan p, int32_t tof_mode, const jp_tof* t, uint64_t* out, void* stream);
 
 /* total number of kernels this library has launched in the process */
 uint64_t jp_launch_count(void);
 
 /*
  * jp_back_tof_lm_noalloc -- TOF listmode back projection that allocates
- * nothing, for callers that cannot allocate device memory: code running
- * while a CUDA graph is being captured, where an allocation is not allowed;
- * engines whose device memory is fully handed out by their own pool or a
- * fixed real-time budget; and callbacks where cudaMalloc would stall the
- * whole device.  The paper has no counterpart; it is a service variant of
- * jp_back_lors (tof_mode 2) with the same arguments and result
- * (img_accum += A^T proj, caller order, same tolerance as the other back
- * projections).
+ * nothing, for callers that cannot allocate device memory: engines whose
+ * device memory is fully handed out by their own pool or a fixed real-time
+ * budget, and callbacks or serving loops where a cudaMalloc (which may
+ * synchronise the whole device) is not allowed to run.  The paper has no
+ * counterpart; it is a service variant of jp_back_lors (tof_mode 2) with the
+ * same arguments and result (img_accum += A^T proj, caller order, same
+ * tolerance as the other back projections).
  * Its scratch is a workspace compiled into the library: 2^20 entries of 16
  * bytes (16 MiB), held by every GPU that loads the library until the process
  * exits.  The image must fit it: sum over a of n_a' (n_b + 2)(n_c + 2) <= 2^20
  * with n_a' = n_a rounded up to even (for instance 64 x 64 x 16, or about
- * 70^3), else JP_ERR_ARG.  The first
- * call on a device looks the workspace address up (cudaGetSymbolAddress),
- * so make that first call before any stream capture.  Every call shares the
- * one workspace (it is cleared at the start of each call): calls that
- * overlap on the GPU, on any stream, race and give wrong results.
+ * 70^3), else JP_ERR_ARG.  The first call on a device looks the workspace
+ * address up (cudaGetSymbolAddress, once per device), so make that first
+ * call before any stream capture; the address is kept for the life of the
+ * process, so a device reset (cudaDeviceReset) after that first call is not
+ * supported.  Every call shares the one workspace (it is cleared at the
+ * start of each call): calls that overlap on the GPU, on any stream, race
+ * and give wrong results.
  * Errors: JP_ERR_ARG, JP_ERR_ALIGN, JP_ERR_CUDA.
  */
 int jp_back_tof_lm_noalloc(const float* xstart, const float* xend, const int16_t* tof_bin,

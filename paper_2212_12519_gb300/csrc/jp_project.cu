@@ -1345,7 +1345,9 @@ int direct(int mode, bool back, const float* xs, const float* xe, const int16_t*
   return fail(JP_ERR_ARG, "bad mode");
 }
 
-// per-LOR count of visited plane samples (same setup as the projectors)
+// per-LOR count of visited plane samples (same setup as the projectors);
+// MODE 1: TOF-sinogram bin evaluations, the bins of every visited sample's
+// window (the sinogram kernels' per-bin work)
 template <int MODE>
 __global__ void count_kernel(const ProjParams p, unsigned long long* out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1368,10 +1370,175 @@ __global__ void count_kernel(const ProjParams p, unsigned long long* out) {
       r.k1 = (int)hi;
       live = lo <= hi;
     }
-    if (live) cnt = (unsigned long long)(r.k1 - r.k0 + 1);
+    if (live && MODE != 1) cnt = (unsigned long long)(r.k1 - r.k0 + 1);
+    if (live && MODE == 1) {
+      const DevTof& T = p.tof;
+      const float delta = p.perm_in_rec ? 0.f : A.w;
+      for (int k = r.k0; k <= r.k1; ++k) {
+        const float tau = fmaf((float)k - r.kc, r.dt, r.tc);
+        const float x = (tau - delta) * T.inv_w + T.hbin;
+        const int t0 = max(0, (int)ceilf(x - T.R_over_w));
+        const int t1 = min(T.nbins - 1, (int)floorf(x + T.R_over_w));
+        if (t0 <= t1) cnt += (unsigned long long)(t1 - t0 + 1);
+      }
+    }
   }
   for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
   if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(out, cnt);
+}
+
+// Throughput ceiling of the TOF-sinogram kernels' per-bin work, on
+// synthetic sample positions: the bins of each window through the
+// bin-aligned table (one shared-memory table read and an interpolation per
+// bin), accumulated into the thread's shared-memory bins (DIR 0, the
+// forward's operation) or multiplied with the thread's shared-memory values
+// and summed (DIR 1, the back projection's); *bins counts the bins done.
+template <int DIR>
+__global__ void bench_tof_bins_kernel(const DevTof T, int per_thread, unsigned long long* bins, float* sink) {
+  extern __shared__ float4 smem4[];
+  float2* lut = reinterpret_cast<float2*>(smem4);
+  float* acc = reinterpret_cast<float*>(lut + kLut) + threadIdx.x;
+  build_lut_aligned(lut, T);
+  const int N = T.nbins;
+  for (int t = 0; t < N; ++t) acc[t * blockDim.x] = DIR ? 1.f : 0.f;
+  __syncthreads();
+  uint32_t h = (blockIdx.x * blockDim.x + threadIdx.x) * 2654435761u + 12345u;
+  unsigned long long nb = 0;
+  float sy = 0.f;
+  for (int it = 0; it < per_thread; ++it) {
+    h = h * 1664525u + 1013904223u;
+    const float x = (float)(h >> 8) * (1.0f / 16777216.0f) * (float)N - 0.5f;  // position in bins
+    const int t0 = max(0, (int)ceilf(x - T.R_over_w));
+    const int t1 = min(N - 1, (int)floorf(x + T.R_over_w));
+    const float dlo = (x - T.hbin) * T.width - ((float)t0 - T.hbin) * T.width;
+    const float xl0 = (dlo + T.Rp) * T.inv_hp;
+    const int ix0 = min(max((int)xl0, 0), T.nodes_a - 1);
+    const float fr = xl0 - (float)ix0;
+    const float sv = 1.f + 1e-3f * x;
+    float* a = acc + t0 * blockDim.x;
+    for (int t = 0, ix = ix0; t <= t1 - t0; ++t, ix -= T.m, a += blockDim.x) {
+      const float2 e = lut[max(ix, 0)];
+      if (DIR == 0) *a = fmaf(fmaf(fr, e.y, e.x), sv, *a);
+      else sy = fmaf(fmaf(fr, e.y, e.x), *a, sy);
+    }
+    nb += (unsigned long long)max(t1 - t0 + 1, 0);
+  }
+  if (DIR == 0)
+    for (int t = 0; t < N; ++t) sy += acc[t * blockDim.x];
+  if (sy == 1234.5f) sink[blockIdx.x] = sy;  // keeps the work
+  for (int o = 16; o > 0; o >>= 1) nb += __shfl_down_sync(0xffffffffu, nb, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(bins, nb);
+}
+
+// L2 reduction requests of the quad-image group back projection
+// (group_kernel<MODE, true, *, G>), counted by replaying its schedule: the
+// same 32-LOR warp chunks, the same lane -> (LOR, plane) map and the same
+// quad entries, with every LOR live (a back-projection input without
+// zeros).  A warp's 16-byte vector reductions coalesce per instruction into
+// one request per 32-byte sector and lane slot: a sector holds two quad
+// entries (planes 2m, 2m+1), so it costs max(lanes on the even entry, lanes
+// on the odd one) requests.
+template <int MODE, int G>
+__global__ void red_count_kernel(const ProjParams p, unsigned long long* out) {
+  constexpr int E = 32 / G;
+  const int lane = threadIdx.x & 31;
+  const int grp = lane / G, gl = lane - grp * G;
+  const DevTof& T = p.tof;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  unsigned long long cnt = 0;
+  for (int64_t chunk = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); chunk * 32 < p.n;
+       chunk += warps) {
+    const int64_t base = chunk * 32;
+    const int64_t i = base + lane;
+    Ray r;
+    r.k0 = 1; r.k1 = 0;
+    int slot = 0;
+    if (i < p.n) {
+      const float4 A = __ldcs(p.lor + 2 * i);
+      const float4 B = __ldcs(p.lor + 2 * i + 1);
+      const float xs[3] = {A.x, A.y, A.z};
+      const float xe[3] = {B.x, B.y, B.z};
+      const float delta = p.perm_in_rec ? 0.f : A.w;
+      const int f = (p.n_frames > 1) ? frame_of(p.frame_off, p.n_frames, i) : 0;
+      slot = p.shared ? 0 : f;
+      bool live = ray_setup(xs, xe, p.g, r);
+      if (MODE == 2 && live) {
+        float ke, Re;
+        event_tof(p, i, ke, Re);
+        const float d0 = r.tc - ((float)__float_as_int(B.w) * T.width + delta);
+        const float t1 = (-Re - d0) / r.dt, t2 = (Re - d0) / r.dt;
+        const float lo = fmaxf(ceilf(r.kc + fminf(t1, t2)), (float)r.k0);
+        const float hi = fminf(floorf(r.kc + fmaxf(t1, t2)), (float)r.k1);
+        r.k0 = (int)lo;
+        r.k1 = (int)hi;
+        live = lo <= hi;
+      }
+      if (!live) { r.k0 = 1; r.k1 = 0; }
+    } else {
+      r.a = 0; r.uc = r.du = r.wc = r.dw = 0.f;
+    }
+#pragma unroll 1
+    for (int pass = 0; pass < G; ++pass) {
+      const int src = pass * E + grp;
+      const int k0 = __shfl_sync(0xffffffffu, r.k0, src);
+      const int k1 = __shfl_sync(0xffffffffu, r.k1, src);
+      const int a = __shfl_sync(0xffffffffu, r.a, src);
+      const int sl = __shfl_sync(0xffffffffu, slot, src);
+      const float uc = __shfl_sync(0xffffffffu, r.uc, src);
+      const float du = __shfl_sync(0xffffffffu, r.du, src);
+      const float wc = __shfl_sync(0xffffffffu, r.wc, src);
+      const float dw = __shfl_sync(0xffffffffu, r.dw, src);
+      const int na = sel3(a, p.g.n[0], p.g.n[1], p.g.n[2]);
+      const int nap = sel3(a, p.ql.nap[0], p.ql.nap[1], p.ql.nap[2]);
+      const int nb = (a == 0) ? p.g.n[1] : p.g.n[0];
+      const int nc = (a == 2) ? p.g.n[1] : p.g.n[2];
+      const int nc2 = nc + 2;
+      const float kc = 0.5f * (float)(na - 1);
+      const float ub = (float)nb, wb = (float)nc;
+      const int64_t qoff = (int64_t)sl * p.ql.slot + sel3(a, p.ql.base[0], p.ql.base[1], p.ql.base[2]);
+      // iterations of the group's plane loop, k = (k0 & ~1) + gl + G s
+      const int kfirst = (k0 & ~1) + gl;
+      const int nit = (k0 <= k1 && kfirst <= k1) ? (k1 - kfirst) / G + 1 : 0;
+      const int maxit = __reduce_max_sync(0xffffffffu, nit);
+      for (int s = 0; s < maxit; ++s) {
+        const int k = kfirst + G * s;
+        const bool active = s < nit && k >= k0;
+        int64_t entry = 0;
+        if (active) {
+          const float kk = (float)k - kc;
+          const float u = fminf(fmaxf(fmaf(kk, du, uc), -1.f), ub);
+          const float w = fminf(fmaxf(fmaf(kk, dw, wc), -1.f), wb);
+          entry = qoff + (((int)floorf(u) + 1) * nc2 + ((int)floorf(w) + 1)) * nap + k;
+        }
+        const unsigned am = __ballot_sync(0xffffffffu, active);
+        const unsigned odd = __ballot_sync(0xffffffffu, active && (entry & 1));
+        if (active) {
+          const unsigned ms = __match_any_sync(am, (unsigned long long)(entry >> 1));
+          if (lane == __ffs(ms) - 1) {
+            const int no = __popc(ms & odd), ne = __popc(ms) - no;
+            cnt += (unsigned long long)max(no, ne);
+          }
+        }
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+  if (lane == 0 && cnt) atomicAdd(out, cnt);
+}
+
+template <int MODE>
+int launch_red_count(const ProjParams& p, int lpw, unsigned long long* out, cudaStream_t st) {
+  const int grid = aux_grid((p.n + 31) / 32 * 32, 256);
+  switch (lpw) {
+    case 1: red_count_kernel<MODE, 32><<<grid, 256, 0, st>>>(p, out); break;
+    case 2: red_count_kernel<MODE, 16><<<grid, 256, 0, st>>>(p, out); break;
+    case 8: red_count_kernel<MODE, 4><<<grid, 256, 0, st>>>(p, out); break;
+    case 16: red_count_kernel<MODE, 2><<<grid, 256, 0, st>>>(p, out); break;
+    default: red_count_kernel<MODE, 8><<<grid, 256, 0, st>>>(p, out); break;
+  }
+  count_launch();
+  JP_TRY_CUDA(cudaGetLastError());
+  return JP_OK;
 }
 
 }  // namespace
@@ -1379,18 +1546,51 @@ __global__ void count_kernel(const ProjParams p, unsigned long long* out) {
 
 using namespace jp;
 
-extern "C" int jp_count_samples(jp_plan pl, int32_t mode, const jp_tof* t, uint64_t* out, void* stream) {
+extern "C" int jp_count_red_requests(jp_plan pl, int32_t mode, const jp_tof* t, uint64_t* out, void* stream) {
   clear_error();
   if (!pl || !out) return fail(JP_ERR_ARG, "NULL argument");
   if (mode != 0 && mode != 2) return fail(JP_ERR_ARG, "mode must be 0 or 2");
   if (!aligned(out, 8)) return fail(JP_ERR_ALIGN, "out must be 8-byte aligned");
   if (mode == 2 && !pl->has_tof_bin) return fail(JP_ERR_STATE, "TOF listmode needs a plan created with tof_bin");
+  int lpw = pl->opts.lors_per_warp;
+  if (lpw == 0) lpw = 4;
+  if (lpw == 32 || (pl->opts.flags & (JP_PLAN_TILES | JP_PLAN_INTERLEAVED)))
+    return fail(JP_ERR_STATE, "the plan's back projection does not run the quad-image group kernel");
   ProjParams p;
   std::memset(&p, 0, sizeof(p));
   int rc = make_geom(&pl->g, &p.g);
   if (rc) return rc;
   if (mode == 2) {
     rc = make_tof(t, false, &p.tof);
+    if (rc) return rc;
+  }
+  p.lor = pl->lor;
+  p.n = pl->n;
+  p.frame_off = pl->frame_off_dev;
+  p.n_frames = pl->n_frames;
+  p.ql = pl->ql;
+  p.shared = 0;  // frames with their own image slots: the launch with the largest footprint
+  p.perm_in_rec = pl->has_delta ? 0 : 1;
+  if (mode == 2 && pl->has_sigma) p.sig = pl->sig_binned;
+  cudaStream_t st = (cudaStream_t)stream;
+  JP_TRY_CUDA(cudaMemsetAsync(out, 0, sizeof(uint64_t), st));
+  if (p.n == 0) return JP_OK;
+  return mode == 0 ? launch_red_count<0>(p, lpw, (unsigned long long*)out, st)
+                   : launch_red_count<2>(p, lpw, (unsigned long long*)out, st);
+}
+
+extern "C" int jp_count_samples(jp_plan pl, int32_t mode, const jp_tof* t, uint64_t* out, void* stream) {
+  clear_error();
+  if (!pl || !out) return fail(JP_ERR_ARG, "NULL argument");
+  if (mode < 0 || mode > 2) return fail(JP_ERR_ARG, "mode must be 0, 1 or 2");
+  if (!aligned(out, 8)) return fail(JP_ERR_ALIGN, "out must be 8-byte aligned");
+  if (mode == 2 && !pl->has_tof_bin) return fail(JP_ERR_STATE, "TOF listmode needs a plan created with tof_bin");
+  ProjParams p;
+  std::memset(&p, 0, sizeof(p));
+  int rc = make_geom(&pl->g, &p.g);
+  if (rc) return rc;
+  if (mode != 0) {
+    rc = make_tof(t, mode == 1, &p.tof);
     if (rc) return rc;
   }
   p.lor = pl->lor;
@@ -1402,8 +1602,56 @@ extern "C" int jp_count_samples(jp_plan pl, int32_t mode, const jp_tof* t, uint6
   if (p.n == 0) return JP_OK;
   unsigned blocks = (unsigned)((p.n + 255) / 256);
   if (mode == 0) count_kernel<0><<<blocks, 256, 0, st>>>(p, (unsigned long long*)out);
+  else if (mode == 1) count_kernel<1><<<blocks, 256, 0, st>>>(p, (unsigned long long*)out);
   else count_kernel<2><<<blocks, 256, 0, st>>>(p, (unsigned long long*)out);
   count_launch();
+  JP_TRY_CUDA(cudaGetLastError());
+  return JP_OK;
+}
+
+extern "C" int jp_bench_tof_bins(const jp_tof* t, int32_t direction, int32_t per_thread, float* ms_out,
+                                 uint64_t* bins_out, void* stream) {
+  clear_error();
+  if (!ms_out || !bins_out || per_thread < 1 || (direction != 0 && direction != 1))
+    return fail(JP_ERR_ARG, "bad arguments");
+  if (!aligned(bins_out, 8)) return fail(JP_ERR_ALIGN, "bins_out must be 8-byte aligned");
+  DevTof T;
+  int rc = make_tof(t, true, &T);
+  if (rc) return rc;
+  if (T.user || T.m <= 0) return fail(JP_ERR_ARG, "needs a Gaussian kernel with a bin-aligned table");
+  const int block = 256;
+  const size_t smem = (size_t)kLut * sizeof(float2) + (size_t)T.nbins * block * sizeof(float);
+  cudaStream_t st = (cudaStream_t)stream;
+  auto k0 = bench_tof_bins_kernel<0>;
+  auto k1 = bench_tof_bins_kernel<1>;
+  rc = prepare_smem(k0, smem);
+  if (rc) return rc;
+  rc = prepare_smem(k1, smem);
+  if (rc) return rc;
+  int per_sm = 0;
+  JP_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, direction ? k1 : k0, block, smem));
+  const int grid = sm_count() * (per_sm < 1 ? 1 : per_sm);
+  float* sink = nullptr;
+  JP_TRY_CUDA(cudaMemsetAsync(bins_out, 0, sizeof(uint64_t), st));
+  // warm-up launch (its bins are counted, then cleared)
+  if (direction) k1<<<grid, block, smem, st>>>(T, per_thread, (unsigned long long*)bins_out, sink);
+  else k0<<<grid, block, smem, st>>>(T, per_thread, (unsigned long long*)bins_out, sink);
+  count_launch();
+  JP_TRY_CUDA(cudaMemsetAsync(bins_out, 0, sizeof(uint64_t), st));
+  cudaEvent_t a, b;
+  JP_TRY_CUDA(cudaEventCreate(&a));
+  JP_TRY_CUDA(cudaEventCreate(&b));
+  JP_TRY_CUDA(cudaEventRecord(a, st));
+  if (direction) k1<<<grid, block, smem, st>>>(T, per_thread, (unsigned long long*)bins_out, sink);
+  else k0<<<grid, block, smem, st>>>(T, per_thread, (unsigned long long*)bins_out, sink);
+  count_launch();
+  JP_TRY_CUDA(cudaEventRecord(b, st));
+  JP_TRY_CUDA(cudaEventSynchronize(b));
+  float ms = 0.f;
+  JP_TRY_CUDA(cudaEventElapsedTime(&ms, a, b));
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  *ms_out = ms;
   JP_TRY_CUDA(cudaGetLastError());
   return JP_OK;
 }

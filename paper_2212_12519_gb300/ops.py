@@ -81,6 +81,8 @@ _SIGS = {
     "jp_osem_ratio_sino": [P, P, P, P, I64, P],
     "jp_sum_f64": [P, I64, P, P],
     "jp_count_samples": [P, I32, P, P, P],
+    "jp_count_red_requests": [P, I32, P, P, P],
+    "jp_bench_tof_bins": [P, I32, I32, P, P, P],
     "jp_osem_subset_tof_lm": [P, I32, I32, P, P, F32, F32, P, P],
     "jp_osem_init": [P, P, I64, P],
     "jp_osem_subset_tof_lm_dev": [P, I32, I32, P, P, F32, P, P, P],
@@ -448,7 +450,8 @@ def jp_back_lors(xs, xe, proj, geom, img_accum, tof_mode="nontof", tof=None, tof
 def jp_back_tof_lm_noalloc(xs, xe, proj, geom, img_accum, tof, tof_bin, delta=None, stream=None):
     """img_accum += A^T proj (TOF listmode) without any device allocation:
     the workspace is fixed inside the library (images up to
-    sum_a n_a (n_b+2)(n_c+2) <= 2^20).  Overlapping calls race."""
+    sum_a n_a' (n_b+2)(n_c+2) <= 2^20, n_a' = n_a rounded up to even).
+    Overlapping calls race."""
     pxs, pxe = _lors(xs, xe)
     g = image_geom(geom)
     t = tof_params(tof)
@@ -605,12 +608,36 @@ def jp_sum_f64(x, out=None, stream=None):
 
 
 def jp_count_samples(plan: Plan, tof_mode="nontof", tof=None, stream=None) -> int:
-    """Plane samples visited by the projector for the plan's LORs (exact)."""
+    """Plane samples visited by the projector for the plan's LORs (exact);
+    tof_mode "tof_sino": the TOF bin evaluations over those samples."""
     out = torch.zeros((), dtype=torch.int64, device="cuda")
     t = tof_params(tof) if tof is not None else None
     _check(load().jp_count_samples(plan.handle, TOF_MODES[tof_mode], ctypes.byref(t) if t is not None else None,
                                    _ptr(out, None, "out"), _stream(stream)))
     return int(out.item())
+
+
+def jp_count_red_requests(plan: Plan, tof_mode="nontof", tof=None, stream=None) -> int:
+    """L2 reduction requests (32-byte sector operations) of the plan's
+    quad-image back projection with every LOR live (device-side replay)."""
+    out = torch.zeros((), dtype=torch.int64, device="cuda")
+    t = tof_params(tof) if tof is not None else None
+    _check(load().jp_count_red_requests(plan.handle, TOF_MODES[tof_mode], ctypes.byref(t) if t is not None else None,
+                                        _ptr(out, None, "out"), _stream(stream)))
+    return int(out.item())
+
+
+def jp_bench_tof_bins(tof, direction: int = 0, per_thread: int = 256, stream=None) -> dict:
+    """Ceiling of the TOF-sinogram per-bin work (measurement helper): bin
+    evaluations per second of the forward's (direction 0) or the back
+    projection's (direction 1) table-and-accumulate operation."""
+    ms = ctypes.c_float()
+    out = torch.zeros((), dtype=torch.int64, device="cuda")
+    t = tof_params(tof)
+    _check(load().jp_bench_tof_bins(ctypes.byref(t), int(direction), int(per_thread), ctypes.byref(ms),
+                                    _ptr(out, None, "bins"), _stream(stream)))
+    bins = int(out.item())
+    return {"bins_per_s": bins / (ms.value / 1e3), "ms": ms.value, "bins": bins, "direction": int(direction)}
 
 
 def jp_bench_red(n_entries: int = 3_000_000, per_thread: int = 64, iters: int = 5, pattern: int = 0,
