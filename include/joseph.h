@@ -204,6 +204,10 @@ int jp_plan_rebind(jp_plan p, const float* xstart, const float* xend, const int1
  * LORs are binned, so the plan is the one jp_plan_create_batch /
  * jp_plan_rebind would build from the gathered coordinates, bit for bit.
  * An index outside [0, n_det) gives the empty LOR (xs = xe = 0: no samples).
+ * The plan keeps a copy of the table padded to 16 bytes per detector (16 *
+ * n_det bytes for the creating call's n_det), refilled on every bind so that
+ * each endpoint costs one 16-byte read; a rebind with more detectors than
+ * that reads det_xyz itself (the same plan, a slower bind).
  * Other arguments and errors as jp_plan_create_batch / jp_plan_rebind; also
  * JP_ERR_ARG for n_det < 1 or NULL detector arrays with n_total > 0.
  */

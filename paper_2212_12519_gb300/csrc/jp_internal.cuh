@@ -339,6 +339,8 @@ struct jp_plan_s {
   uint32_t* keys;         // [capacity]
   uint32_t* hist;         // [frame_capacity * keys_per_frame + 1]
   uint32_t* block_sums;   // scan scratch
+  float4* det4;           // [det4_cap] detector table padded to 16 bytes (detector-index plans)
+  int32_t det4_cap;
   int64_t* frame_off_dev; // [frame_capacity + 1]
   int64_t* frame_off_host;// pinned [frame_capacity + 1]
   int64_t hist_len;

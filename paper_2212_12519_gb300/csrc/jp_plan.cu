@@ -45,6 +45,7 @@ struct KeyParams {
   const int32_t* ds;
   const int32_t* de;
   const float* dxyz;
+  const float4* det4;  // the plan's 16-byte-padded copy of dxyz, or NULL
   int32_t n_det;
   const int16_t* tof_bin;
   const float* delta;
@@ -57,6 +58,9 @@ struct KeyParams {
   // wide in-plane direction whichever axis holds the scanner's axial one);
   // the axial-offset key takes the remaining axis c = 3 - a - b
   int kb[3];
+  // per image axis: the centre plane's coordinate, and key cells per
+  // (padded) index unit of the offset, window and axial-offset keys
+  float xc[3], inv_cell_u[3], inv_cell_w[3], inv_cell_z[3];
   int slope_bins, offset_bins, window_bins, zoff_bins, keys_per_frame;
   float tof_width;  // > 0: listmode window binning
   int keep_order;
@@ -65,26 +69,88 @@ struct KeyParams {
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
+// Where the endpoints come from: the coordinate arrays, the caller's
+// [n_det][3] detector table, or the plan's 16-byte-padded copy of it.
+enum { kSrcXyz = 0, kSrcDet = 1, kSrcDet4 = 2 };
+
+// detector coordinates of index d; an index outside [0, n_det) gives the
+// origin (so a LOR with one gives the empty LOR xs = xe = 0)
+template <int SRC>
+__device__ __forceinline__ void det_xyz(const KeyParams& p, int32_t d, bool ok, float x[3]) {
+  if (SRC == kSrcDet4) {
+    const float4 v = ok ? __ldg(p.det4 + d) : make_float4(0.f, 0.f, 0.f, 0.f);
+    x[0] = v.x;
+    x[1] = v.y;
+    x[2] = v.z;
+  } else {
+    const float* q = p.dxyz + 3 * (int64_t)(ok ? d : 0);
+    for (int i = 0; i < 3; ++i) x[i] = ok ? __ldg(q + i) : 0.f;
+  }
+}
+
 // endpoints of caller LOR j, from the coordinate arrays or from the detector
 // table; an index outside [0, n_det) gives the empty LOR xs = xe = 0
+template <int SRC>
 __device__ __forceinline__ void lor_endpoints(const KeyParams& p, int64_t j, float xs[3], float xe[3]) {
-  if (p.dxyz) {
+  if (SRC != kSrcXyz) {
     const int32_t a = __ldg(p.ds + j), b = __ldg(p.de + j);
     const bool ok = (unsigned)a < (unsigned)p.n_det && (unsigned)b < (unsigned)p.n_det;
-    const float* pa = p.dxyz + 3 * (int64_t)(ok ? a : 0);
-    const float* pb = p.dxyz + 3 * (int64_t)(ok ? b : 0);
-    for (int i = 0; i < 3; ++i) {
-      xs[i] = ok ? __ldg(pa + i) : 0.f;
-      xe[i] = ok ? __ldg(pb + i) : 0.f;
-    }
+    det_xyz<SRC>(p, a, ok, xs);
+    det_xyz<SRC>(p, b, ok, xe);
   } else {
     for (int i = 0; i < 3; ++i) {
-      xs[i] = p.xs[3 * j + i];
-      xe[i] = p.xe[3 * j + i];
+      xs[i] = __ldg(p.xs + 3 * j + i);
+      xe[i] = __ldg(p.xe + 3 * j + i);
     }
   }
 }
 
+// The packed records of PER LORs j[q] (entries with j[q] >= n are zero):
+// (xs, w), (xe, tof_bin bits), w = delta[j] when with_delta, else the
+// caller index j.  Every load is issued before the caller's stores (the
+// detector-table reads after the index reads), so a thread keeps all of its
+// LORs' loads in flight at once.
+template <int SRC, int PER>
+__device__ __forceinline__ void load_records(const KeyParams& p, const int64_t (&j)[PER], bool with_delta,
+                                             float4 (&ra)[PER], float4 (&rb)[PER]) {
+  int32_t da[PER], db[PER];
+  float w[PER];
+  int tb[PER];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const bool in = j[q] < p.n;
+    da[q] = (in && SRC != kSrcXyz) ? __ldg(p.ds + j[q]) : 0;
+    db[q] = (in && SRC != kSrcXyz) ? __ldg(p.de + j[q]) : 0;
+    w[q] = (in && with_delta) ? __ldg(p.delta + j[q]) : __int_as_float((int)j[q]);
+    tb[q] = (in && p.tof_bin) ? (int)__ldg(p.tof_bin + j[q]) : 0;
+  }
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const bool in = j[q] < p.n;
+    float xs[3] = {0.f, 0.f, 0.f}, xe[3] = {0.f, 0.f, 0.f};
+    if (SRC != kSrcXyz) {
+      const bool ok = in && (unsigned)da[q] < (unsigned)p.n_det && (unsigned)db[q] < (unsigned)p.n_det;
+      det_xyz<SRC>(p, da[q], ok, xs);
+      det_xyz<SRC>(p, db[q], ok, xe);
+    } else if (in) {
+      for (int i = 0; i < 3; ++i) {
+        xs[i] = __ldg(p.xs + 3 * j[q] + i);
+        xe[i] = __ldg(p.xe + 3 * j[q] + i);
+      }
+    }
+    ra[q] = make_float4(xs[0], xs[1], xs[2], w[q]);
+    rb[q] = make_float4(xe[0], xe[1], xe[2], __int_as_float(tb[q]));
+  }
+}
+
+// one 32-byte store: a record fills its sector in a single request
+__device__ __forceinline__ void st_record(float4* dst, float4 a, float4 b) {
+  asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(dst), "f"(a.x), "f"(a.y), "f"(a.z),
+               "f"(a.w), "f"(b.x), "f"(b.y), "f"(b.z), "f"(b.w)
+               : "memory");
+}
+
+template <int SRC>
 __global__ void key_kernel(KeyParams p, uint32_t* __restrict__ keys, uint32_t* __restrict__ hist) {
   int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= p.n) return;
@@ -92,44 +158,42 @@ __global__ void key_kernel(KeyParams p, uint32_t* __restrict__ keys, uint32_t* _
   uint32_t key = 0;
   if (!p.keep_order) {
     float xs[3], xe[3];
-    lor_endpoints(p, j, xs, xe);
+    lor_endpoints<SRC>(p, j, xs, xe);
     const float d0 = xe[0] - xs[0], d1 = xe[1] - xs[1], d2 = xe[2] - xs[2];
     const int a = principal_axis(xs, xe);
-    const int b = p.kb[a];
+    const int b = sel3(a, p.kb[0], p.kb[1], p.kb[2]);
     const DevGeom& g = p.g;
     const float da = sel3(a, d0, d1, d2), db = sel3(b, d0, d1, d2);
-    const float sb = (da != 0.f) ? db / da : 0.f;  // in [-1, 1]
+    // the keys only order the LORs, so reciprocals stand in for divisions
+    const float rda = (da != 0.f) ? __frcp_rn(da) : 0.f;
+    const float sb = db * rda;  // in [-1, 1]
     const int qs = clampi((int)floorf((sb + 1.f) * 0.5f * (float)p.slope_bins), 0, p.slope_bins - 1);
     // in-plane offset (continuous index along b) where the line crosses the centre plane
-    const int na = sel3(a, g.n[0], g.n[1], g.n[2]), nb = sel3(b, g.n[0], g.n[1], g.n[2]);
     const float oa = sel3(a, g.o[0], g.o[1], g.o[2]), ob = sel3(b, g.o[0], g.o[1], g.o[2]);
-    const float va = sel3(a, g.v[0], g.v[1], g.v[2]), ivb = sel3(b, g.inv_v[0], g.inv_v[1], g.inv_v[2]);
-    const float kc = 0.5f * (float)(na - 1);
-    const float Xc = oa + kc * va;
+    const float ivb = sel3(b, g.inv_v[0], g.inv_v[1], g.inv_v[2]);
     const float ma = 0.5f * (sel3(a, xs[0], xs[1], xs[2]) + sel3(a, xe[0], xe[1], xe[2]));
     const float mb = 0.5f * (sel3(b, xs[0], xs[1], xs[2]) + sel3(b, xe[0], xe[1], xe[2]));
-    const float t = (da != 0.f) ? (Xc - ma) / da : 0.f;
+    const float t = (sel3(a, p.xc[0], p.xc[1], p.xc[2]) - ma) * rda;
     const float u = (fmaf(t, db, mb) - ob) * ivb;
-    const float cell_u = (float)(nb + 2) / (float)p.offset_bins;
-    const int qu = clampi((int)floorf((u + 1.f) / cell_u), 0, p.offset_bins - 1);
+    const int qu = clampi((int)floorf((u + 1.f) * sel3(b, p.inv_cell_u[0], p.inv_cell_u[1], p.inv_cell_u[2])), 0,
+                          p.offset_bins - 1);
     int qw = 0;
     if (p.window_bins > 1 && p.tof_width > 0.f && p.tof_bin != nullptr) {
-      const float L = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+      const float L2 = d0 * d0 + d1 * d1 + d2 * d2;
       const float cen = (float)p.tof_bin[j] * p.tof_width + (p.delta ? p.delta[j] : 0.f);
-      const float ca = (L > 0.f) ? ma + cen * da / L : ma;  // window centre along a
-      const float ka = (ca - oa) / va;
-      const float cell_a = (float)(na + 2) / (float)p.window_bins;
-      qw = clampi((int)floorf((ka + 1.f) / cell_a), 0, p.window_bins - 1);
+      const float ca = (L2 > 0.f) ? fmaf(cen * da, rsqrtf(L2), ma) : ma;  // window centre along a
+      const float ka = (ca - oa) * sel3(a, g.inv_v[0], g.inv_v[1], g.inv_v[2]);
+      qw = clampi((int)floorf((ka + 1.f) * sel3(a, p.inv_cell_w[0], p.inv_cell_w[1], p.inv_cell_w[2])), 0,
+                  p.window_bins - 1);
     }
     int qz = 0;
     if (p.zoff_bins > 1) {
       const int c = 3 - a - b;
-      const int nc = sel3(c, g.n[0], g.n[1], g.n[2]);
       const float oc = sel3(c, g.o[0], g.o[1], g.o[2]), ivc = sel3(c, g.inv_v[0], g.inv_v[1], g.inv_v[2]);
       const float mc = 0.5f * (sel3(c, xs[0], xs[1], xs[2]) + sel3(c, xe[0], xe[1], xe[2]));
       const float w = (fmaf(t, sel3(c, d0, d1, d2), mc) - oc) * ivc;
-      const float cell_w = (float)(nc + 2) / (float)p.zoff_bins;
-      qz = clampi((int)floorf((w + 1.f) / cell_w), 0, p.zoff_bins - 1);
+      qz = clampi((int)floorf((w + 1.f) * sel3(c, p.inv_cell_z[0], p.inv_cell_z[1], p.inv_cell_z[2])), 0,
+                  p.zoff_bins - 1);
     }
     key = (uint32_t)((((a * p.slope_bins + qs) * p.offset_bins + qu) * p.window_bins + qw) * p.zoff_bins + qz);
   }
@@ -222,35 +286,41 @@ __global__ void scan_apply_kernel(uint32_t* __restrict__ data, int64_t n, const 
   }
 }
 
-// Each thread places kScatterPer LORs; their slot claims are independent
-// returning atomics, so several are in flight at once (the claims, not the
-// bandwidth, bound this kernel).
+// Each thread places kScatterPer LORs: it issues all their input loads,
+// then their slot claims (independent returning atomics), then one 32-byte
+// record store each, so every thread keeps several LORs in flight.
 constexpr int kScatterPer = 4;
 
+template <int SRC>
 __global__ void scatter_kernel(KeyParams p, const uint32_t* __restrict__ keys, uint32_t* __restrict__ cursor,
                                float4* __restrict__ lor, int32_t* __restrict__ perm) {
   const int64_t base = ((int64_t)blockIdx.x * blockDim.x) * kScatterPer + threadIdx.x;
-  uint32_t pos[kScatterPer];
+  int64_t j[kScatterPer];
+  uint32_t key[kScatterPer], pos[kScatterPer];
 #pragma unroll
   for (int q = 0; q < kScatterPer; ++q) {
-    const int64_t j = base + (int64_t)q * blockDim.x;
-    pos[q] = 0;
-    if (j < p.n) pos[q] = p.keep_order ? (uint32_t)j : atomicAdd(cursor + keys[j], 1u);
+    j[q] = base + (int64_t)q * blockDim.x;
+    key[q] = (!p.keep_order && j[q] < p.n) ? __ldg(keys + j[q]) : 0u;
   }
+  // without TOF centre offsets the caller index rides in the record, so a
+  // LOR costs one scattered 32-byte sector instead of two
+  float4 ra[kScatterPer], rb[kScatterPer];
+  load_records<SRC, kScatterPer>(p, j, p.delta != nullptr, ra, rb);
+#pragma unroll
+  for (int q = 0; q < kScatterPer; ++q)
+    pos[q] = (j[q] < p.n) ? (p.keep_order ? (uint32_t)j[q] : atomicAdd(cursor + key[q], 1u)) : 0u;
 #pragma unroll
   for (int q = 0; q < kScatterPer; ++q) {
-    const int64_t j = base + (int64_t)q * blockDim.x;
-    if (j >= p.n) continue;
-    // without TOF centre offsets the caller index rides in the record, so a
-    // LOR costs one scattered 32-byte sector instead of two
-    const float w0 = p.delta ? p.delta[j] : __int_as_float((int)j);
-    const int tb = p.tof_bin ? (int)p.tof_bin[j] : 0;
-    float xs[3], xe[3];
-    lor_endpoints(p, j, xs, xe);
-    lor[2 * (int64_t)pos[q]] = make_float4(xs[0], xs[1], xs[2], w0);
-    lor[2 * (int64_t)pos[q] + 1] = make_float4(xe[0], xe[1], xe[2], __int_as_float(tb));
-    if (p.delta) perm[pos[q]] = (int32_t)j;
+    if (j[q] >= p.n) continue;
+    st_record(lor + 2 * (int64_t)pos[q], ra[q], rb[q]);
+    if (p.delta) perm[pos[q]] = (int32_t)j[q];
   }
+}
+
+// padded copy of the detector table: one 16-byte load per endpoint
+__global__ void det4_fill_kernel(const float* __restrict__ xyz, int32_t n_det, float4* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n_det) out[i] = make_float4(xyz[3 * (int64_t)i], xyz[3 * (int64_t)i + 1], xyz[3 * (int64_t)i + 2], 0.f);
 }
 
 // Frame offsets reach the device as kernel arguments (copied at launch), so
@@ -356,6 +426,12 @@ int bind(jp_plan p, const float* xs, const float* xe, const int16_t* tof_bin, co
   kp.xs = det ? nullptr : xs; kp.xe = det ? nullptr : xe;
   kp.ds = det ? det->ds : nullptr; kp.de = det ? det->de : nullptr;
   kp.dxyz = det ? det->xyz : nullptr; kp.n_det = det ? det->n_det : 0;
+  kp.det4 = nullptr;
+  if (det && p->det4 && det->n_det <= p->det4_cap) {
+    det4_fill_kernel<<<(det->n_det + 255) / 256, 256, 0, st>>>(det->xyz, det->n_det, p->det4);
+    count_launch();
+    kp.det4 = p->det4;
+  }
   kp.tof_bin = tof_bin; kp.delta = delta; kp.n = n;
   kp.frame_off = p->frame_off_dev; kp.n_frames = n_frames; kp.g = g;
   for (int a = 0; a < 3; ++a) {
@@ -363,6 +439,13 @@ int bind(jp_plan p, const float* xs, const float* xe, const int16_t* tof_bin, co
     const double e0 = (double)g.n[b0] * g.v[b0], e1 = (double)g.n[b1] * g.v[b1];
     kp.kb[a] = (e1 > e0) ? b1 : b0;
     p->kb[a] = kp.kb[a];
+  }
+  for (int a = 0; a < 3; ++a) {
+    const float cells = (float)(g.n[a] + 2);
+    kp.xc[a] = g.o[a] + 0.5f * (float)(g.n[a] - 1) * g.v[a];
+    kp.inv_cell_u[a] = (float)p->dims.offset_bins / cells;
+    kp.inv_cell_w[a] = (float)p->dims.window_bins / cells;
+    kp.inv_cell_z[a] = (float)p->dims.zoff_bins / cells;
   }
   kp.slope_bins = p->dims.slope_bins; kp.offset_bins = p->dims.offset_bins;
   kp.window_bins = p->dims.window_bins; kp.zoff_bins = p->dims.zoff_bins;
@@ -376,7 +459,9 @@ int bind(jp_plan p, const float* xs, const float* xe, const int16_t* tof_bin, co
   if (!kp.keep_order) {
     JP_TRY_CUDA(cudaMemsetAsync(p->hist, 0, sizeof(uint32_t) * hist_len, st));
   }
-  key_kernel<<<blocks, 256, 0, st>>>(kp, p->keys, p->hist);
+  const int src = kp.det4 ? kSrcDet4 : (kp.dxyz ? kSrcDet : kSrcXyz);
+  auto key_k = src == kSrcDet4 ? key_kernel<kSrcDet4> : (src == kSrcDet ? key_kernel<kSrcDet> : key_kernel<kSrcXyz>);
+  key_k<<<blocks, 256, 0, st>>>(kp, p->keys, p->hist);
   count_launch();
   JP_TRY_CUDA(cudaGetLastError());
   if (!kp.keep_order) {
@@ -389,7 +474,9 @@ int bind(jp_plan p, const float* xs, const float* xe, const int16_t* tof_bin, co
     count_launch();
     JP_TRY_CUDA(cudaGetLastError());
   }
-  scatter_kernel<<<(unsigned)((n + 256 * kScatterPer - 1) / (256 * kScatterPer)), 256, 0, st>>>(
+  auto scatter_k = src == kSrcDet4 ? scatter_kernel<kSrcDet4>
+                                   : (src == kSrcDet ? scatter_kernel<kSrcDet> : scatter_kernel<kSrcXyz>);
+  scatter_k<<<(unsigned)((n + 256 * kScatterPer - 1) / (256 * kScatterPer)), 256, 0, st>>>(
       kp, p->keys, p->hist, p->lor, p->perm);
   count_launch();
   axis_flags_kernel<<<(n_frames * 3 + 127) / 128, 128, 0, st>>>(p->hist, n_frames, p->dims.keys_per_frame,
@@ -407,6 +494,7 @@ void free_plan(jp_plan p) {
   cudaFree(p->keys);
   cudaFree(p->hist);
   cudaFree(p->block_sums);
+  cudaFree(p->det4);
   cudaFree(p->frame_off_dev);
   cudaFreeHost(p->frame_off_host);
   cudaFree(p->quads);
@@ -496,6 +584,10 @@ static int create_batch(jp_plan* out, const float* xs, const float* xe, const in
   if (e == cudaSuccess) e = cudaMalloc(&p->keys, sizeof(uint32_t) * nn);
   if (e == cudaSuccess) e = cudaMalloc(&p->hist, sizeof(uint32_t) * (p->hist_len + 1));
   if (e == cudaSuccess) e = cudaMalloc(&p->block_sums, sizeof(uint32_t) * (p->scan_blocks_cap + 1));
+  if (e == cudaSuccess && det && det->n_det > 0) {
+    e = cudaMalloc(&p->det4, sizeof(float4) * (size_t)det->n_det);
+    p->det4_cap = det->n_det;
+  }
   if (e == cudaSuccess) e = cudaMalloc(&p->frame_off_dev, sizeof(int64_t) * (n_frames + 1));
   if (e == cudaSuccess) e = cudaMallocHost(&p->frame_off_host, sizeof(int64_t) * (n_frames + 1));
   p->quad_slots = interleaved ? 2 : std::max<int32_t>(n_frames, 1);

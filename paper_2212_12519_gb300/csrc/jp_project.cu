@@ -113,6 +113,14 @@ int make_tof(const jp_tof* t, bool sino, DevTof* out) {
 
 namespace {
 
+// Two consecutive plane-fastest quad entries (planes 2m, 2m+1 of one quad
+// row, 32-byte aligned) in one 32-byte read-only load.
+__device__ __forceinline__ void ld_quad_pair(const float4* q, float4& a, float4& b) {
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+      : "l"(q));
+}
+
 // ---------------------------------------------------------------------------
 // planned projection kernel: persistent CTAs over binned LORs, quad images
 // ---------------------------------------------------------------------------
@@ -177,7 +185,51 @@ __global__ void __launch_bounds__(kMaxBlock) planned_kernel(const ProjParams p) 
       if (MODE == 1)
         for (int t = 0; t < N; ++t) acc[t * blockDim.x] = 0.f;
       float sum = 0.f;
-      if (live) {
+      if (MODE == 0 && live && p.kfast) {
+        // plane-fastest quads: planes 2m and 2m+1 of a quad row share one
+        // 32-byte sector, so two samples that stay in their quad row take a
+        // single 32-byte load (the sum keeps the plane order).  Non-TOF
+        // only: in TOF listmode the extra registers cost a fifth of the
+        // resident warps and the forward gets slower (5.27 vs 5.18 ms on a
+        // 40M-event frame; non-TOF 8.18 vs 8.40 ms)
+        auto coords = [&](int kq, float& kk, float& al, float& be, int& ip, int& jq) {
+          kk = (float)kq - r.kc;
+          const float u = fminf(fmaxf(fmaf(kk, r.du, r.uc), -1.f), ub);
+          const float w = fminf(fmaxf(fmaf(kk, r.dw, r.wc), -1.f), wb);
+          const float fu = floorf(u), fw = floorf(w);
+          al = u - fu;
+          be = w - fw;
+          ip = (int)fu + 1;
+          jq = (int)fw + 1;
+        };
+        auto add = [&](float al, float be, float4 v) {
+          const float top = fmaf(be, v.z - v.x, v.x);
+          const float bot = fmaf(be, v.w - v.y, v.y);
+          sum += fmaf(al, bot - top, top);
+        };
+        auto load1 = [&](int kq, int ip, int jq) { return __ldg(Q + quad_index(true, kq, ip, jq, na, nb2, nc2)); };
+        int k = r.k0;
+        float kk0, al0, be0, kk1, al1, be1;
+        int ip0, jq0, ip1, jq1;
+        if (k & 1) {
+          coords(k, kk0, al0, be0, ip0, jq0);
+          add(al0, be0, load1(k, ip0, jq0));
+          ++k;
+        }
+        for (; k < r.k1; k += 2) {
+          coords(k, kk0, al0, be0, ip0, jq0);
+          coords(k + 1, kk1, al1, be1, ip1, jq1);
+          float4 v0, v1;
+          ld_quad_pair(Q + quad_index(true, k, ip0, jq0, na, nb2, nc2), v0, v1);
+          if (ip1 != ip0 || jq1 != jq0) v1 = load1(k + 1, ip1, jq1);
+          add(al0, be0, v0);
+          add(al1, be1, v1);
+        }
+        if (k == r.k1) {
+          coords(k, kk0, al0, be0, ip0, jq0);
+          add(al0, be0, load1(k, ip0, jq0));
+        }
+      } else if (live) {
         for (int k = r.k0; k <= r.k1; ++k) {
           const float kk = (float)k - r.kc;
           const float u = fminf(fmaxf(fmaf(kk, r.du, r.uc), -1.f), ub);
