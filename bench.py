@@ -823,9 +823,9 @@ def run_profile_tof_sino(args):
 
 def run_profile_case(args):
     """One frame of --events listmode events (200x200x71, TOF unless
-    --lm-mode nontof): the plan (key, scan x3, scatter, flags), then three
-    times forward + back projection (each timed with CUDA events), then a
-    rebind."""
+    --lm-mode nontof; from coordinates, or with --det from detector indices):
+    the plan (key, scan x3, scatter, flags), then three times forward + back
+    projection (each timed with CUDA events), then a rebind."""
     from paper_2212_12519_gb300 import build as jbuild, ops, synth
     jbuild.build()
     ops.load()
@@ -833,15 +833,24 @@ def run_profile_case(args):
     g, tof = synth.GEOM_CLINICAL, synth.TOF_CLINICAL
     nontof = args.lm_mode == "nontof"
     ph = synth.ellipsoid_phantom(g, synth.PHANTOM_CLINICAL, 4001, device=dev)
-    xs, xe, tb = synth.lm_events(ph, g, synth.SCANNER_CLINICAL, tof, args.events, seed=4051, device=dev)
+    xs, xe, tb, ds, de = synth.lm_events(ph, g, synth.SCANNER_CLINICAL, tof, args.events, seed=4051, device=dev,
+                                         return_det=True)
+    det = synth.SCANNER_CLINICAL.crystal_table(dev)
     y = torch.rand(args.events, device=dev)
     img = torch.zeros(g.shape, device=dev)
     popts = plan_opts(args)
-    if nontof:
+    tb_arg = None if nontof else tb
+    if args.det:
+        # listmode as recorded: detector-index pairs and the detector table
+        plan = ops.jp_plan_create_batch_det(ds, de, det, g, [0, args.events], tof_bin=tb_arg,
+                                            tof_bin_width=0.0 if nontof else tof.bin_width, **popts)
+    elif nontof:
         plan = ops.jp_plan_create(xs, xe, g, **popts)
-        fwd, back = (lambda: ops.jp_fwd(plan, ph)), (lambda: ops.jp_back(plan, y, img))
     else:
         plan = ops.jp_plan_create(xs, xe, g, tof_bin=tb, tof_bin_width=tof.bin_width, **popts)
+    if nontof:
+        fwd, back = (lambda: ops.jp_fwd(plan, ph)), (lambda: ops.jp_back(plan, y, img))
+    else:
         fwd, back = (lambda: ops.jp_fwd_tof_lm(plan, ph, tof)), (lambda: ops.jp_back_tof_lm(plan, y, tof, img))
     ms = {"fwd": [], "back": []}
     for _ in range(3):
@@ -851,10 +860,14 @@ def run_profile_case(args):
             fn()
             b.record()
             ms[name].append((a, b))
-    ops.jp_plan_rebind(plan, xs, xe, tof_bin=None if nontof else tb)
+    if args.det:
+        ops.jp_plan_rebind_det(plan, ds, de, det, [0, args.events], tof_bin=tb_arg)
+    else:
+        ops.jp_plan_rebind(plan, xs, xe, tof_bin=tb_arg)
     torch.cuda.synchronize()
     mode = "nontof" if nontof else "tof_lm"
-    print(json.dumps({"profile_case": mode, "events": args.events, "path": args.path, "plan_opts": popts,
+    print(json.dumps({"profile_case": mode, "events": args.events, "det": bool(args.det), "path": args.path,
+                      "plan_opts": popts,
                       "ms": {k: [a.elapsed_time(b) for a, b in v] for k, v in ms.items()},
                       "samples": ops.jp_count_samples(plan, mode, tof)}))
     plan.destroy()
@@ -1091,6 +1104,8 @@ def main():
     ap.add_argument("--ref-events", type=int, default=400_000)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--det", action="store_true",
+                    help="profile_case: bind the events from detector indices and the detector table")
     ap.add_argument("--e2e-buffers", type=int, default=3,
                     help="device input buffer sets of the end-to-end pipeline (>= 2)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
