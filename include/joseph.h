@@ -98,7 +98,8 @@ typedef struct {
  * LORs of a warp walk nearly the same voxels (paper Sec. 4 suggests event
  * pre-sorting; Sec. 2.6 and 3 show the memory-order sensitivity it removes). */
 typedef struct {
-  int32_t block;          /* threads per CTA for projections (0 = 256; 64..512, multiple of 32) */
+  int32_t block;          /* threads per CTA for projections (64..512, multiple of 32; 0 = 256,
+                             except 512 for the TOF-sinogram forward) */
   int32_t slope_bins;     /* bins over the in-plane slope d_b/d_a in [-1,1] (0 = 128) */
   int32_t offset_bins;    /* bins over the in-plane offset at the central plane (0 = 256) */
   int32_t window_bins;    /* bins over the TOF-window centre along the principal
@@ -458,7 +459,8 @@ int jp_count_samples(jp_plan p, int32_t tof_mode, const jp_tof* t, uint64_t* out
  * accumulated into per-thread shared-memory bins (direction 0, the
  * forward's operation) or dotted with per-thread shared-memory values
  * (direction 1, the back projection's), per_thread samples per thread on
- * every resident thread of the GPU.  *ms_out (host) is the time of one
+ * every resident thread of the GPU, in CTAs of the projection's default
+ * size (512 threads forward, 256 back).  *ms_out (host) is the time of one
  * timed launch after a warm-up one, *bins_out (device uint64) the bins it
  * evaluated.  Synchronises the stream.  Errors: JP_ERR_ARG, JP_ERR_ALIGN,
  * JP_ERR_CUDA. */

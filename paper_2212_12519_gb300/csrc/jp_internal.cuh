@@ -330,6 +330,7 @@ struct jp_plan_s {
   int32_t n_frames;
   jp_image_geom g;
   jp_plan_opts opts;
+  bool auto_block;        // opts.block was 0: each kernel takes its own default
   jp::PlanDims dims;
   bool has_tof_bin, has_delta;
   int kb[3];              // per principal axis: the in-plane axis of the slope / offset keys

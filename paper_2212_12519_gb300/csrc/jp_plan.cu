@@ -534,6 +534,7 @@ static int create_batch(jp_plan* out, const float* xs, const float* xe, const in
   jp_plan_opts o;
   std::memset(&o, 0, sizeof(o));
   if (opts) o = *opts;
+  const bool auto_block = (o.block == 0);
   if (o.block == 0) o.block = 256;
   if (o.block < 64 || o.block > 512 || (o.block % 32) != 0) return fail(JP_ERR_ARG, "opts.block must be 64..512, multiple of 32");
   if (o.slope_bins == 0) o.slope_bins = 128;
@@ -560,6 +561,7 @@ static int create_batch(jp_plan* out, const float* xs, const float* xe, const in
   p->frame_capacity = n_frames;
   p->g = *g;
   p->opts = o;
+  p->auto_block = auto_block;
   p->dims.slope_bins = o.slope_bins;
   p->dims.offset_bins = o.offset_bins;
   p->dims.window_bins = window_bins;

@@ -125,7 +125,7 @@ __device__ __forceinline__ void ld_quad_pair(const float4* q, float4& a, float4&
 // planned projection kernel: persistent CTAs over binned LORs, quad images
 // ---------------------------------------------------------------------------
 template <int MODE, bool BACK, bool LUT>
-__global__ void __launch_bounds__(kMaxBlock) planned_kernel(const ProjParams p) {
+__global__ void __launch_bounds__(kMaxBlock, (MODE == 1 && !BACK) ? 3 : 1) planned_kernel(const ProjParams p) {
   extern __shared__ float4 smem4[];
   float2* lut = reinterpret_cast<float2*>(smem4);
   float* accbase = reinterpret_cast<float*>(lut + ((MODE != 0 && LUT) ? kLut : 0));
@@ -1300,7 +1300,10 @@ int planned(jp_plan pl, int mode, bool back, const float* in, float* out, int64_
   // a tabulated kernel always goes through the shared-memory table; a
   // per-event sigma takes the exact path (the table holds one sigma)
   const bool lut = (mode != 0) && ((!(pl->opts.flags & JP_PLAN_TOF_EXACT) && !p.sig) || p.tof.user);
-  const int block = pick_block(pl->opts.block, mode, p.tof, lut);
+  // the TOF-sinogram forward's default is 512 threads (three CTAs of 512 keep
+  // 48 warps resident, its shared-memory accumulators allow no more)
+  const int block = pick_block((pl->auto_block && mode == 1 && !back) ? kMaxBlock : pl->opts.block, mode, p.tof,
+                               lut);
   cudaStream_t st = (cudaStream_t)stream;
   int lpw = pl->opts.lors_per_warp;
   const bool sorted = !(pl->opts.flags & (JP_PLAN_KEEP_ORDER | JP_PLAN_INTERLEAVED));
@@ -1671,7 +1674,11 @@ extern "C" int jp_bench_tof_bins(const jp_tof* t, int32_t direction, int32_t per
   int rc = make_tof(t, true, &T);
   if (rc) return rc;
   if (T.user || T.m <= 0) return fail(JP_ERR_ARG, "needs a Gaussian kernel with a bin-aligned table");
-  const int block = 256;
+  // the CTA size of the projection it stands for: 512 threads for the
+  // forward, 256 for the back projection, and 256 when 512 threads' bins
+  // would not fit in shared memory
+  int block = direction ? 256 : kMaxBlock;
+  if ((size_t)kLut * sizeof(float2) + (size_t)T.nbins * block * sizeof(float) > 96 * 1024) block = 256;
   const size_t smem = (size_t)kLut * sizeof(float2) + (size_t)T.nbins * block * sizeof(float);
   cudaStream_t st = (cudaStream_t)stream;
   auto k0 = bench_tof_bins_kernel<0>;

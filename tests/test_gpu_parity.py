@@ -396,3 +396,35 @@ def test_detector_index_plans(ops, clinical_img):
     assert fwd_err(f2, p_or2, amb2) <= FWD_TOL
     pd.destroy()
     pc.destroy()
+
+
+def test_detector_table_read_paths(ops, clinical_img):
+    """The plan reads detector coordinates from its 16-byte-padded copy of
+    the table when the table fits the copy made at creation, else from the
+    caller's [n_det][3] table; both give the coordinate plan's forward bit
+    for bit (a plan created from coordinates and rebound to detector input,
+    and a detector plan rebound to a larger table, take the second path)."""
+    g = synth.GEOM_CLINICAL
+    tof = synth.TOF_CLINICAL
+    sc = synth.SCANNER_CLINICAL
+    xs, xe, tb, ds, de = synth.lm_events(torch.from_numpy(clinical_img), g, sc, tof, 80_003, seed=4611,
+                                         return_det=True)
+    table = sc.crystal_table("cuda")
+    # the table followed by 100 unused entries: more detectors than a plan
+    # created with `table` holds in its padded copy
+    big = torch.cat([table, torch.zeros((100, 3), device="cuda")]).contiguous()
+    img = cuda(clinical_img)
+    ds_c, de_c, tb_c = ds.cuda(), de.cuda(), tb.cuda()
+    ref_plan = ops.jp_plan_create(xs.cuda(), xe.cuda(), g, tof_bin=tb_c, tof_bin_width=tof.bin_width)
+    ref = ops.jp_fwd_tof_lm(ref_plan, img, tof)
+    padded = ops.jp_plan_create_batch_det(ds_c, de_c, table, g, [0, len(xs)], tof_bin=tb_c,
+                                          tof_bin_width=tof.bin_width)
+    assert torch.equal(ops.jp_fwd_tof_lm(padded, img, tof), ref)
+    ops.jp_plan_rebind_det(padded, ds_c, de_c, big, tof_bin=tb_c)  # n_det above the copy: the caller's table
+    assert torch.equal(ops.jp_fwd_tof_lm(padded, img, tof), ref)
+    ops.jp_plan_rebind_det(padded, ds_c, de_c, table, tof_bin=tb_c)  # back to the copy
+    assert torch.equal(ops.jp_fwd_tof_lm(padded, img, tof), ref)
+    ops.jp_plan_rebind_det(ref_plan, ds_c, de_c, table, tof_bin=tb_c)  # coordinate plan: no copy
+    assert torch.equal(ops.jp_fwd_tof_lm(ref_plan, img, tof), ref)
+    padded.destroy()
+    ref_plan.destroy()
