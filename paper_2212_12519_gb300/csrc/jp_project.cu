@@ -124,8 +124,12 @@ __device__ __forceinline__ void ld_quad_pair(const float4* q, float4& a, float4&
 // ---------------------------------------------------------------------------
 // planned projection kernel: persistent CTAs over binned LORs, quad images
 // ---------------------------------------------------------------------------
+// The TOF-sinogram forward is compiled for three resident CTAs of 512 (40
+// registers); the other instances keep the compiler's own register choice
+// (a minimum of 0 CTAs states none: 1 would let the TOF-listmode forward
+// grow from 48 to 54 registers and lose a fifth of its resident warps).
 template <int MODE, bool BACK, bool LUT>
-__global__ void __launch_bounds__(kMaxBlock, (MODE == 1 && !BACK) ? 3 : 1) planned_kernel(const ProjParams p) {
+__global__ void __launch_bounds__(kMaxBlock, (MODE == 1 && !BACK) ? 3 : 0) planned_kernel(const ProjParams p) {
   extern __shared__ float4 smem4[];
   float2* lut = reinterpret_cast<float2*>(smem4);
   float* accbase = reinterpret_cast<float*>(lut + ((MODE != 0 && LUT) ? kLut : 0));
