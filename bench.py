@@ -302,7 +302,7 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = run_e2e(args, W, plan, g, tof, dev, ws, nontof)
     # L2 reduction ceiling (one 16-byte RED per plane sample bounds the back projection)
-    red = {pt: ops.jp_bench_red(pattern=pt) for pt in (0, 1, 2)}
+    red = {pt: ops.jp_bench_red(pattern=pt) for pt in (0, 1, 2, 3, 4)}
     cpu_sample = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu_sample = _oracle_events(W, min(W["xs"].shape[0], 8_000_000))
@@ -356,6 +356,7 @@ def run_ours(args):
                          "traffic": (BACK_DRAM_BYTES_PER_EVENT * n_total if not nontof else None),
                          "requests_per_launch": requests, "requests_per_sample": requests / max(samples, 1),
                          "peak_patterns": {str(k): v["sectors_per_s"] for k, v in red.items()},
+                         "lane_reductions_per_s_patterns": {str(k): v["reductions_per_s"] for k, v in red.items()},
                          "peak_source": "jp_bench_red_pattern (measured in this run), max over patterns"},
             "hbm_roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved,
                              "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],

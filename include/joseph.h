@@ -524,7 +524,9 @@ int jp_bench_red(float* buf, int64_t n_entries, int32_t per_thread, int32_t iter
 /* Same, with an access pattern: 0 = every lane its own random 16-byte entry
  * (one 32-byte L2 sector per reduction), 1 = pairs of lanes on the two
  * halves of one random sector, 2 = a warp on 32 consecutive entries (512
- * contiguous bytes).  Pattern 0 is jp_bench_red. */
+ * contiguous bytes), 3 / 4 = groups of 4 / 8 lanes on the first 4 / 8
+ * entries of one random 128-byte line (how much sharing lines, not only
+ * sectors, saves).  Pattern 0 is jp_bench_red. */
 int jp_bench_red_pattern(float* buf, int64_t n_entries, int32_t per_thread, int32_t iters, int32_t pattern,
                          float* ms_out, void* stream);
 

@@ -157,6 +157,10 @@ __global__ void bench_red_kernel(float4* buf, uint32_t n, int per_thread, int pa
       i = (mix32((t >> 1) * 131u + (uint32_t)r) % (n / 2)) * 2u + (lane & 1u);
     } else if (pattern == 2) {
       i = (mix32(warp * 131u + (uint32_t)r) % (n / 32)) * 32u + lane;
+    } else if (pattern == 3 || pattern == 4) {
+      // L = 4 or 8 lanes on the first L entries of one random 128-byte line
+      const uint32_t L = pattern == 3 ? 4u : 8u;
+      i = (mix32((t / L) * 131u + (uint32_t)r) % (n / 8)) * 8u + (lane % L);
     } else {
       i = mix32(t * 131u + (uint32_t)r) % n;
     }
@@ -336,7 +340,7 @@ extern "C" int jp_bench_red_pattern(float* buf, int64_t n_entries, int32_t per_t
                                     int32_t pattern, float* ms_out, void* stream) {
   clear_error();
   if (!buf || !ms_out || n_entries < 64 || n_entries > (int64_t)UINT32_MAX || per_thread < 1 || iters < 1 ||
-      pattern < 0 || pattern > 2)
+      pattern < 0 || pattern > 4)
     return fail(JP_ERR_ARG, "bad arguments");
   if (!aligned(buf, 16)) return fail(JP_ERR_ALIGN, "buf must be 16-byte aligned");
   cudaStream_t st = (cudaStream_t)stream;

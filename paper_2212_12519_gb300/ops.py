@@ -645,14 +645,15 @@ def jp_bench_red(n_entries: int = 3_000_000, per_thread: int = 64, iters: int = 
     """Scattered 16-byte reduction ceiling of the device (measurement helper):
     reductions per second over an L2-resident buffer of n_entries float4.
     pattern 0: one random sector per reduction; 1: two reductions per random
-    sector; 2: a warp on 512 contiguous bytes."""
+    sector; 2: a warp on 512 contiguous bytes; 3 / 4: 4 / 8 lanes on one
+    random 128-byte line."""
     buf = torch.zeros((n_entries, 4), dtype=torch.float32, device="cuda")
     ms = ctypes.c_float()
     _check(load().jp_bench_red_pattern(_ptr(buf, torch.float32, "buf"), int(n_entries), int(per_thread),
                                        int(iters), int(pattern), ctypes.byref(ms), _stream(stream)))
     blocks = torch.cuda.get_device_properties(buf.device).multi_processor_count * 32
     ops_ = blocks * 256 * per_thread
-    sectors_per_red = {0: 1.0, 1: 0.5, 2: 0.5}[int(pattern)]
+    sectors_per_red = {0: 1.0, 1: 0.5, 2: 0.5, 3: 0.5, 4: 0.5}[int(pattern)]
     rate = ops_ / (ms.value / 1e3)
     return {"reductions_per_s": rate, "sectors_per_s": rate * sectors_per_red, "ms": ms.value,
             "buffer_bytes": n_entries * 16, "pattern": int(pattern)}

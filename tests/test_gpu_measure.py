@@ -71,3 +71,13 @@ def test_red_requests_bounds_on_listmode(ops):
     r2 = ops.jp_count_red_requests(plan, "tof_lm", tof)
     assert abs(r2 - r) <= 0.01 * r  # only the order of equal keys changes
     plan.destroy()
+
+
+def test_bench_red_patterns(ops):
+    """The reduction ceiling benchmark runs every access pattern and rejects
+    an unknown one."""
+    for pt in range(5):
+        r = ops.jp_bench_red(n_entries=1 << 16, per_thread=4, iters=1, pattern=pt)
+        assert r["reductions_per_s"] > 0 and r["sectors_per_s"] > 0
+    with pytest.raises(ops.JosephError):
+        ops.jp_bench_red(n_entries=1 << 16, per_thread=4, iters=1, pattern=5)
