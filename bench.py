@@ -38,7 +38,7 @@ UNIT = "events/s"
 # kernel on one 10M-event frame, 200x200x71), scaled to a launch by its
 # events: the traffic grows with the events; the per-frame image terms are
 # small.
-BACK_DRAM_BYTES_PER_EVENT = (608_469_248 + 76_418_304) / 10_000_000
+BACK_DRAM_BYTES_PER_EVENT = (606_467_072 + 77_018_880) / 10_000_000
 
 
 # ---------------------------------------------------------------------------
