@@ -307,13 +307,19 @@ def run_ours(args):
     if rank == 0 and not args.no_cpu_baseline:
         cpu_sample = _oracle_events(W, min(W["xs"].shape[0], 8_000_000))
     plan.destroy()
+    extra_nontof = None
+    if not args.no_extra and rank == 0 and ws == 1 and not nontof:
+        # the same events without their TOF bins, while they are resident
+        extra_nontof = measure_nontof_lm_batch(W, 5, 3)
     del W["xs"], W["xe"], W["ds"], W["de"], W["w"], W["bvec"]
     W["tb"] = None
     torch.cuda.empty_cache()
     workloads = None
     if not args.no_extra and rank == 0 and ws == 1 and not nontof:
-        # the other workloads at one GPU: configs 2 and 3 and the paper's 34-subset iteration
-        workloads = {name: measure_sino(name, 5, 3) for name in ("sino_clinical", "tof_sino")}
+        # the other workloads at one GPU: the three sinogram configurations,
+        # non-TOF listmode and the paper's 34-subset iteration
+        workloads = {name: measure_sino(name, 5, 3) for name in ("sino_small", "sino_clinical", "tof_sino")}
+        workloads["nontof_lm"] = extra_nontof
         workloads["lm_osem_iter"] = measure_lm_osem_iter(5, 3, args.fwhm)
     serving = None
     if not args.no_serving and rank == 0 and not nontof:
@@ -373,6 +379,51 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def measure_nontof_lm_batch(W, steps, warmup):
+    """Non-TOF listmode on the batch's events (their TOF bins dropped): one
+    step is the rebind from detector indices, the forward projection, the
+    Poisson loss with a background of 10% of each frame's mean projection
+    and its backward (the back projection), as the TOF step."""
+    from paper_2212_12519_gb300 import ops
+    from paper_2212_12519_gb300.autograd import JosephNonTOF, PoissonLogLik
+    g = W["geom"]
+    n_frames = len(W["offsets"]) - 1
+    epf = W["offsets"][1]
+    plan = ops.jp_plan_create_batch_det(W["ds"], W["de"], W["det"], g, W["offsets"])
+    p0 = ops.jp_fwd(plan, W["x"]).view(n_frames, epf).mean(dim=1)
+    bframe = (0.1 * p0).float().contiguous()
+    del p0
+    x = W["x"].clone().requires_grad_(True)
+
+    def step():
+        ops.jp_plan_rebind_det(plan, W["ds"], W["de"], W["det"], W["offsets"])
+        x.grad = None
+        p = JosephNonTOF.apply(x, plan)
+        loss = PoissonLogLik.apply(p, plan, W["w"], bframe)
+        loss.backward()
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        step()
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    samples = ops.jp_count_samples(plan, "nontof")
+    n = W["ds"].shape[0]
+    plan.destroy()
+    del x
+    return {"metric": "non-TOF listmode fwd+back events/s", "value": n / (ms / 1e3), "unit": UNIT,
+            "ms_per_step": ms, "steps": steps, "warmup": warmup, "higher_is_better": True,
+            "samples_per_step": samples,
+            "config": {"workload": f"nontof_lm_batch{n_frames}x{epf // 1_000_000}M_200x200x71",
+                       "input": "the TOF batch's detector-index pairs without their TOF bins",
+                       "step": "bin + fwd + loss + back"}}
 
 
 def run_e2e(args, W, plan, g, tof, dev, ws, nontof=False):
