@@ -78,10 +78,11 @@ enum { kSrcXyz = 0, kSrcDet = 1, kSrcDet4 = 2 };
 template <int SRC>
 __device__ __forceinline__ void det_xyz(const KeyParams& p, int32_t d, bool ok, float x[3]) {
   if (SRC == kSrcDet4) {
-    const float4 v = ok ? __ldg(p.det4 + d) : make_float4(0.f, 0.f, 0.f, 0.f);
-    x[0] = v.x;
-    x[1] = v.y;
-    x[2] = v.z;
+    // the index is clamped too, so no form of the load leaves the table
+    const float4 v = __ldg(p.det4 + (ok ? d : 0));
+    x[0] = ok ? v.x : 0.f;
+    x[1] = ok ? v.y : 0.f;
+    x[2] = ok ? v.z : 0.f;
   } else {
     const float* q = p.dxyz + 3 * (int64_t)(ok ? d : 0);
     for (int i = 0; i < 3; ++i) x[i] = ok ? __ldg(q + i) : 0.f;
