@@ -445,3 +445,12 @@ def test_detector_table_read_paths(ops, clinical_img):
     assert torch.equal(ops.jp_fwd_tof_lm(ref_plan, img, tof), ref)
     padded.destroy()
     ref_plan.destroy()
+    # non-TOF plans (no TOF bins) from detector indices, both table paths
+    ref_plan = ops.jp_plan_create(xs.cuda(), xe.cuda(), g)
+    ref = ops.jp_fwd(ref_plan, img)
+    padded = ops.jp_plan_create_batch_det(ds_c, de_c, table, g, [0, len(xs)])
+    assert torch.equal(ops.jp_fwd(padded, img), ref)
+    ops.jp_plan_rebind_det(padded, ds_c, de_c, big)
+    assert torch.equal(ops.jp_fwd(padded, img), ref)
+    padded.destroy()
+    ref_plan.destroy()
