@@ -99,7 +99,8 @@ typedef struct {
  * pre-sorting; Sec. 2.6 and 3 show the memory-order sensitivity it removes). */
 typedef struct {
   int32_t block;          /* threads per CTA for projections (64..512, multiple of 32; 0 = 256,
-                             except 512 for the TOF-sinogram forward) */
+                             except 512 for the TOF-sinogram forward and 128 for the
+                             non-TOF and TOF-listmode forwards) */
   int32_t slope_bins;     /* bins over the in-plane slope d_b/d_a in [-1,1] (0 = 128) */
   int32_t offset_bins;    /* bins over the in-plane offset at the central plane (0 = 256) */
   int32_t window_bins;    /* bins over the TOF-window centre along the principal
