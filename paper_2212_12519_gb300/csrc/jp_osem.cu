@@ -89,18 +89,51 @@ __device__ __forceinline__ void block_comp_sum(float& s, float& c) {
   }
 }
 
-// pass 1: each block's compensated partial sum of w_e log(p_e + b_f) into part[block]
+// frame of event i for a thread whose i only grows: the frame [lo, hi) of
+// the previous event is reused until i leaves it (a grid-stride loop crosses
+// a frame boundary once per frame)
+__device__ __forceinline__ int frame_cached(const int64_t* __restrict__ off, int n_frames, int64_t i, int& f,
+                                            int64_t& lo, int64_t& hi) {
+  if (i < lo || i >= hi) {
+    f = frame_of(off, n_frames, i);
+    lo = __ldg(off + f);
+    hi = __ldg(off + f + 1);
+  }
+  return f;
+}
+
+// pass 1: each block's compensated partial sum of w_e log(p_e + b_f) into
+// part[block]; four events per iteration into four independent compensated
+// sums, so the loads and logarithms of an iteration do not wait on the
+// previous sum.
 __global__ void loglik_value_kernel(const float* __restrict__ p, const float* __restrict__ w,
                                     const float* __restrict__ b, const int64_t* __restrict__ off, int n_frames,
                                     int64_t n, float2* __restrict__ part) {
-  float s = 0.f, c = 0.f;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int f = (n_frames > 1) ? frame_of(off, n_frames, i) : 0;
-    const float wi = w ? __ldcs(w + i) : 1.f;
-    comp_merge(s, c, __fmul_rn(wi, logf(__ldcs(p + i) + __ldg(b + f))), 0.f);
+  float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
+  int f = 0;
+  int64_t lo = 0, hi = n_frames > 1 ? 0 : n;  // one frame: never searched
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < n; i += 4 * stride) {
+    float pv[4], wv[4], bv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      pv[q] = __ldcs(p + i + q * stride);
+      wv[q] = w ? __ldcs(w + i + q * stride) : 1.f;
+      bv[q] = __ldg(b + frame_cached(off, n_frames, i + q * stride, f, lo, hi));
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) comp_merge(s[q], c[q], __fmul_rn(wv[q], logf(pv[q] + bv[q])), 0.f);
   }
-  block_comp_sum(s, c);
-  if (threadIdx.x == 0) part[blockIdx.x] = make_float2(s, c);
+  for (; i < n; i += stride) {
+    const float wi = w ? __ldcs(w + i) : 1.f;
+    comp_merge(s[0], c[0], __fmul_rn(wi, logf(__ldcs(p + i) + __ldg(b + frame_cached(off, n_frames, i, f, lo, hi)))),
+               0.f);
+  }
+#pragma unroll
+  for (int q = 1; q < 4; ++q) comp_merge(s[0], c[0], s[q], c[q]);
+  block_comp_sum(s[0], c[0]);
+  if (threadIdx.x == 0) part[blockIdx.x] = make_float2(s[0], c[0]);
 }
 
 // pass 2 (one block): the partials' compensated sum into *out
@@ -115,10 +148,11 @@ __global__ void loglik_grad_kernel(const float* __restrict__ p, const float* __r
                                    const float* __restrict__ b, const int64_t* __restrict__ off, int n_frames,
                                    const float* __restrict__ scale, int64_t n, float* __restrict__ g) {
   const float sc = scale ? __ldg(scale) : 1.f;
+  int f = 0;
+  int64_t lo = 0, hi = n_frames > 1 ? 0 : n;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int f = (n_frames > 1) ? frame_of(off, n_frames, i) : 0;
     const float wi = w ? __ldcs(w + i) : 1.f;
-    __stcs(g + i, sc * wi / (__ldcs(p + i) + __ldg(b + f)));
+    __stcs(g + i, sc * wi / (__ldcs(p + i) + __ldg(b + frame_cached(off, n_frames, i, f, lo, hi))));
   }
 }
 
